@@ -1,0 +1,30 @@
+"""FP64 CPU oracle for the all-at-once Runge--Kutta heat-equation solver.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product package may import, call,
+link or execute anything in this directory; only the tests, the smoke check
+of the build entry point and the CPU-baseline leg of the benchmark use it.
+
+It is a plain, slow, obviously-correct restatement of the method:
+
+* ``tableau``    -- Butcher tableaus (Radau IIA, Gauss--Legendre) by collocation,
+                    stability function, LDU factorisation of A_RK (Sec. 2, Sec. 3).
+* ``operators``  -- finite-difference stiffness K (constant or face-averaged
+                    variable kappa) and mass M = I; Q1 finite-element M and K.
+* ``aao``        -- the all-at-once operator of Eq. (system_all_at_once_RK) with
+                    the blocks Phi, Psi_1, Psi_2, Theta = I (x) Theta_hat, its
+                    transpose, the right-hand side, and a dense Kronecker assembly.
+* ``multigrid``  -- Galerkin geometric multigrid V-cycles for M + cK (stands in
+                    for the closed HSL_MI20 AMG of Sec. 5).
+* ``precond``    -- Rana's stage preconditioner (block LDU reading), inner GMRES
+                    for Theta_tilde, the Schur approximation S_tilde of
+                    Eq. (AppSchur), the block-triangular P_tilde of Eq. (AppPrec),
+                    and their transposes.
+* ``fgmres``     -- restarted right-preconditioned flexible GMRES (Algorithm 1
+                    with P_L = I, P_R = P_tilde).
+* ``sequential`` -- sequential RK time stepping with direct stage solves.
+* ``adjoint``    -- the adjoint solve and gradients of the tracking functional.
+* ``lowprec``    -- round-to-nearest-even storage emulation (bf16/fp16/fp32)
+                    with per-row power-of-two scaling.
+
+Parity status per function is stated in each module header.
+"""
