@@ -1,0 +1,185 @@
+"""Python front end of the C ABI: one `Solver` per heat problem.
+
+Vectors are torch float64 tensors on the GPU (used in place, on the solver's
+stream) or float64 numpy arrays on the host (the library copies them through
+its workspace).  Every operation runs in libaao_rk.so; this module only
+marshals arguments.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from .tableau import make as make_tableau
+
+
+def _ptr(a):
+    """Address of a contiguous float64 torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("numpy vectors must be contiguous float64")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("torch vectors must be contiguous float64")
+        return a.data_ptr()
+    raise TypeError(f"unsupported vector type {type(a)}")
+
+
+@dataclass
+class Info:
+    outer_its: int
+    inner_its_total: int
+    rel_res: float
+    converged: bool
+    t_theta_ms: float
+    t_schur_ms: float
+    t_total_ms: float
+    history: list = field(default_factory=list)
+
+    @staticmethod
+    def from_c(ci: _lib.aao_info) -> "Info":
+        return Info(ci.outer_its, ci.inner_its_total, ci.rel_res, bool(ci.converged), ci.t_theta_ms,
+                    ci.t_schur_ms, ci.t_total_ms, [ci.history[i] for i in range(ci.n_history)])
+
+
+class Solver:
+    """Handle for one problem: grid n (interior points per axis), final time T,
+    nt steps, an RK tableau (A, b, c), optional nodal diffusivity kappa."""
+
+    def __init__(self, n: Sequence[int], T: float, nt: int, tableau=None, method: str = "radau", s: int = 2,
+                 lens=None, kappa=None, prec_P: str = "fp64", prec_Pint: Optional[str] = None,
+                 tol: float = 1e-8, restart: int = 20, maxit: int = 100, inner_maxit: int = 0,
+                 inner_tol: float = -1.0, mg_cycles: int = 3, mg_pre: int = 2, mg_post: int = 2,
+                 mg_omega: float = 0.8, stream=None):
+        self._lib = _lib.lib()
+        self.n = tuple(int(v) for v in n)
+        self.dim = len(self.n)
+        A, b, c = tableau if tableau is not None else make_tableau(method, s)
+        A, b, c = np.asarray(A, float), np.asarray(b, float), np.asarray(c, float)
+        self.s = len(b)
+        self.nt = int(nt)
+        self.tau = float(T) / self.nt
+        g = _lib.aao_grid()
+        g.dim = self.dim
+        for a in range(3):
+            g.n[a] = self.n[a] if a < self.dim else 1
+            g.len[a] = (lens[a] if lens is not None else 1.0) if a < self.dim else 1.0
+        g.disc = _lib.DISC["fd"]
+        self._kappa = kappa     # keep alive until set-up copied it
+        g.kappa = _ptr(kappa)
+        t = _lib.aao_tableau()
+        t.s = self.s
+        for i in range(self.s):
+            for j in range(self.s):
+                t.A[i * self.s + j] = A[i, j]
+            t.b[i] = b[i]
+            t.c[i] = c[i]
+        o = _lib.aao_options()
+        self._lib.aao_rk_default_options(C.byref(o))
+        o.tol, o.restart, o.maxit = tol, restart, maxit
+        o.inner_maxit, o.inner_tol = inner_maxit, inner_tol
+        o.mg_cycles, o.mg_pre, o.mg_post, o.mg_omega = mg_cycles, mg_pre, mg_post, mg_omega
+        o.prec_P = _lib.PREC[prec_P]
+        o.prec_Pint = _lib.PREC[prec_Pint if prec_Pint is not None else prec_P]
+        o.stream = stream
+        self.options = o
+        h = C.c_void_p()
+        _lib.check(self._lib.aao_rk_setup(C.byref(g), self.tau, self.nt, C.byref(t), C.byref(o), C.byref(h)))
+        self.h = h
+        nx, nst = C.c_longlong(), C.c_longlong()
+        _lib.check(self._lib.aao_rk_sizes(h, C.byref(nx), C.byref(nst)))
+        self.nx, self.n_st = nx.value, nst.value
+        self.n_v = (self.nt + 1) * self.nx
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.aao_rk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- operator and preconditioner --------------------------------------------
+    def set_tolerances(self, tol=None, maxit=None, inner_tol=None, restart=None):
+        o = self.options
+        if tol is not None:
+            o.tol = tol
+        if maxit is not None:
+            o.maxit = maxit
+        if inner_tol is not None:
+            o.inner_tol = inner_tol
+        if restart is not None:
+            o.restart = restart
+        _lib.check(self._lib.aao_rk_set_options(self.h, C.byref(o)))
+
+    def rhs(self, f, u0, out, f_time_dep=False):
+        _lib.check(self._lib.aao_rk_rhs(self.h, _ptr(f), int(f_time_dep), _ptr(u0), _ptr(out)))
+        return out
+
+    def matvec(self, x, y, transpose=False):
+        fn = self._lib.aao_rk_matvec_transpose if transpose else self._lib.aao_rk_matvec
+        _lib.check(fn(self.h, _ptr(x), _ptr(y)))
+        return y
+
+    def precond_apply(self, r, z, transpose=False):
+        fn = self._lib.aao_rk_precond_apply_transpose if transpose else self._lib.aao_rk_precond_apply
+        _lib.check(fn(self.h, _ptr(r), _ptr(z)))
+        return z
+
+    def shifted_solve(self, stage, b, x):
+        _lib.check(self._lib.aao_rk_shifted_solve(self.h, int(stage), _ptr(b), _ptr(x)))
+        return x
+
+    def pint_apply(self, r, y, transpose=False):
+        _lib.check(self._lib.aao_rk_pint_apply(self.h, _ptr(r), _ptr(y), int(transpose)))
+        return y
+
+    def inner_solve(self, nblocks, r, z):
+        its = (C.c_int * nblocks)()
+        _lib.check(self._lib.aao_rk_inner_solve(self.h, int(nblocks), _ptr(r), _ptr(z), its))
+        return z, list(its)
+
+    # -- solves ---------------------------------------------------------------------
+    def solve(self, f, u0, x, x0_given=False, f_time_dep=False, allow_not_converged=False):
+        info = _lib.aao_info()
+        _lib.check(self._lib.aao_rk_solve(self.h, _ptr(f), int(f_time_dep), _ptr(u0), _ptr(x), int(x0_given),
+                                          C.byref(info)),
+                   allow=(-4,) if allow_not_converged else ())
+        return x, Info.from_c(info)
+
+    def solve_rhs(self, rhs, x, x0_given=False, allow_not_converged=False):
+        info = _lib.aao_info()
+        _lib.check(self._lib.aao_rk_solve_rhs(self.h, _ptr(rhs), _ptr(x), int(x0_given), C.byref(info)),
+                   allow=(-4,) if allow_not_converged else ())
+        return x, Info.from_c(info)
+
+    def adjoint_solve(self, dJdx, lam, x_fwd=None, grad_f=None, grad_kappa=None, allow_not_converged=False):
+        info = _lib.aao_info()
+        _lib.check(self._lib.aao_rk_adjoint_solve(self.h, _ptr(dJdx), _ptr(lam), _ptr(x_fwd), _ptr(grad_f),
+                                                  _ptr(grad_kappa), C.byref(info)),
+                   allow=(-4,) if allow_not_converged else ())
+        return lam, Info.from_c(info)
+
+
+def solve_batched(solvers, fs, u0s, xs):
+    """One call for many independent problems (aao_rk_solve_batched)."""
+    lib = _lib.lib()
+    n = len(solvers)
+    hs = (C.c_void_p * n)(*[s.h for s in solvers])
+    F = (C.c_void_p * n)(*[_ptr(f) for f in fs])
+    U = (C.c_void_p * n)(*[_ptr(u) for u in u0s])
+    X = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    infos = (_lib.aao_info * n)()
+    _lib.check(lib.aao_rk_solve_batched(n, hs, F, U, X, infos))
+    return [Info.from_c(i) for i in infos]

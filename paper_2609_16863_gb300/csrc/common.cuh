@@ -1,0 +1,268 @@
+// Shared device helpers: precision traits, per-row scaled storage, warp
+// reductions, grid geometry and the finite-difference stiffness stencil.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <string>
+
+#include "aao_rk.h"
+
+namespace aao {
+
+constexpr int kWarp = 32;
+constexpr int kBlock = 256;              // threads per block of every row kernel
+constexpr int kWarpsPerBlock = kBlock / kWarp;
+constexpr int kMaxS = 8;                 // RK stages
+constexpr int kMaxV = 16;                // values per lane of one row: n0 <= 512
+constexpr int kMaxRowLen = kWarp * kMaxV;
+constexpr int kMaxInner = 16;            // inner GMRES iterations
+constexpr int kMaxRestart = 64;          // outer FGMRES restart
+constexpr int kMaxLevels = 16;
+constexpr int kMaxCoarsest = 512;        // unknowns of the dense coarsest solve
+
+// ---------------------------------------------------------------------------
+// Storage precision traits.  Arithmetic is double for FP64 storage and float
+// for every lower precision; 16-bit storage carries one power-of-two scale per
+// grid row (value = stored * scale), chosen so the row maximum is <= 2^14.
+// ---------------------------------------------------------------------------
+template <class S> struct PT;
+template <> struct PT<double> {
+    using A = double;
+    static constexpr bool scaled = false;
+    __device__ static double ld(double v) { return v; }
+    __device__ static double st(double v) { return v; }
+};
+template <> struct PT<float> {
+    using A = float;
+    static constexpr bool scaled = false;
+    __device__ static float ld(float v) { return v; }
+    __device__ static float st(float v) { return v; }
+};
+template <> struct PT<__nv_bfloat16> {
+    using A = float;
+    static constexpr bool scaled = true;
+    __device__ static float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+};
+template <> struct PT<__half> {
+    using A = float;
+    static constexpr bool scaled = true;
+    __device__ static float ld(__half v) { return __half2float(v); }
+    __device__ static __half st(float v) { return __float2half_rn(v); }
+};
+
+// A batched vector in storage type S: item b starts at d + b*bs (elements);
+// rows of n0 contiguous values; sc (scaled types only) holds one float per row.
+template <class S> struct Vec {
+    S* d = nullptr;
+    float* sc = nullptr;
+    long long bs = 0;
+};
+
+// Read-only view of one batch item (or one stage of it) with per-row scales.
+template <class S> struct View {
+    const S* d;
+    const float* sc;
+    int n0;
+    __device__ __forceinline__ typename PT<S>::A at(long long row, int col) const {
+        typename PT<S>::A v = PT<S>::ld(d[row * n0 + col]);
+        if constexpr (PT<S>::scaled) v *= sc[row];
+        return v;
+    }
+};
+
+template <class S>
+__device__ __forceinline__ View<S> view_of(const Vec<S>& v, long long b, long long elem_off, int n0) {
+    View<S> w;
+    long long base = b * v.bs + elem_off;
+    w.d = v.d + base;
+    w.sc = PT<S>::scaled ? v.sc + base / n0 : nullptr;
+    w.n0 = n0;
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <class T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Store one row of n0 values f(col) at out (+ its scale at *out_sc) from one warp.
+template <class S, class F>
+__device__ __forceinline__ void row_store(S* out, float* out_sc, int n0, int lane, F&& f) {
+    if constexpr (PT<S>::scaled) {
+        float v[kMaxV];
+        float m = 0.f;
+#pragma unroll
+        for (int t = 0; t < kMaxV; ++t) {
+            int c = lane + kWarp * t;
+            v[t] = 0.f;
+            if (c < n0) {
+                v[t] = (float)f(c);
+                m = fmaxf(m, fabsf(v[t]));
+            }
+        }
+        m = warp_max(m);
+        int e = 0;
+        float sc = 1.f, inv = 1.f;
+        if (m > 0.f && m <= 3.0e38f) {
+            frexpf(m, &e);                 // m <= 2^e
+            sc = ldexpf(1.f, e - 14);
+            inv = ldexpf(1.f, 14 - e);
+        }
+#pragma unroll
+        for (int t = 0; t < kMaxV; ++t) {
+            int c = lane + kWarp * t;
+            if (c < n0) out[c] = PT<S>::st(v[t] * inv);
+        }
+        if (lane == 0) *out_sc = sc;
+    } else {
+        for (int c = lane; c < n0; c += kWarp) out[c] = PT<S>::st((typename PT<S>::A)f(c));
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void row_store_ptrs(const Vec<S>& v, long long b, long long elem_off,
+                                               long long row, int n0, S*& out, float*& out_sc) {
+    long long base = b * v.bs + elem_off;
+    out = v.d + base + row * n0;
+    out_sc = PT<S>::scaled ? v.sc + base / n0 + row : nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry of one grid level and the FD stiffness K = -div(kappa grad).
+// Rows are (j, k) lines along x: row = j + n1*k, R = n1*n2 rows.
+// Face coefficients (kappa_f / h^2) are optional (nullptr = kappa == 1):
+//   fx[row*(n0+1) + c]       face between x-nodes c-1 and c   (c = 0..n0)
+//   fy[(k*(n1+1) + j)*n0 + c] face between y-nodes j-1 and j   (j = 0..n1)
+//   fz[(k*n1 + j)*n0 + c]     face between z-nodes k-1 and k   (k = 0..n2)
+// ---------------------------------------------------------------------------
+struct Geo {
+    int d;
+    int n0, n1, n2;
+    long long nx;   // n0*n1*n2
+    int R;          // rows n1*n2
+    double hx2, hy2, hz2;   // 1/h^2 per axis
+};
+
+template <class T> struct Faces {
+    const T* fx = nullptr;
+    const T* fy = nullptr;
+    const T* fz = nullptr;
+};
+
+// (K u)_P at column c of row (j,k) of view u.
+template <class S, class T>
+__device__ __forceinline__ typename PT<S>::A fd_K(const View<S>& u, const Geo& g, const Faces<T>& f,
+                                                   long long row, int j, int k, int c) {
+    using A = typename PT<S>::A;
+    A uP = u.at(row, c);
+    A uW = c > 0 ? u.at(row, c - 1) : A(0);
+    A uE = c + 1 < g.n0 ? u.at(row, c + 1) : A(0);
+    A uS = j > 0 ? u.at(row - 1, c) : A(0);
+    A uN = j + 1 < g.n1 ? u.at(row + 1, c) : A(0);
+    A out;
+    if (f.fx == nullptr) {
+        out = A(g.hx2) * (A(2) * uP - uW - uE) + A(g.hy2) * (A(2) * uP - uS - uN);
+        if (g.d == 3) {
+            A uD = k > 0 ? u.at(row - g.n1, c) : A(0);
+            A uU = k + 1 < g.n2 ? u.at(row + g.n1, c) : A(0);
+            out += A(g.hz2) * (A(2) * uP - uD - uU);
+        }
+    } else {
+        const long long fxi = row * (g.n0 + 1) + c;
+        const long long fyi = ((long long)k * (g.n1 + 1) + j) * g.n0 + c;
+        out = A(f.fx[fxi]) * (uP - uW) + A(f.fx[fxi + 1]) * (uP - uE) +
+              A(f.fy[fyi]) * (uP - uS) + A(f.fy[fyi + g.n0]) * (uP - uN);
+        if (g.d == 3) {
+            A uD = k > 0 ? u.at(row - g.n1, c) : A(0);
+            A uU = k + 1 < g.n2 ? u.at(row + g.n1, c) : A(0);
+            const long long fzi = ((long long)k * g.n1 + j) * g.n0 + c;
+            out += A(f.fz[fzi]) * (uP - uD) + A(f.fz[fzi + (long long)g.n1 * g.n0]) * (uP - uU);
+        }
+    }
+    return out;
+}
+
+// Diagonal of K at a point.
+template <class A, class T>
+__device__ __forceinline__ A fd_K_diag(const Geo& g, const Faces<T>& f, long long row, int j, int k, int c) {
+    if (f.fx == nullptr) {
+        A dg = A(2) * A(g.hx2) + A(2) * A(g.hy2);
+        if (g.d == 3) dg += A(2) * A(g.hz2);
+        return dg;
+    }
+    const long long fxi = row * (g.n0 + 1) + c;
+    const long long fyi = ((long long)k * (g.n1 + 1) + j) * g.n0 + c;
+    A dg = A(f.fx[fxi]) + A(f.fx[fxi + 1]) + A(f.fy[fyi]) + A(f.fy[fyi + g.n0]);
+    if (g.d == 3) {
+        const long long fzi = ((long long)k * g.n1 + j) * g.n0 + c;
+        dg += A(f.fz[fzi]) + A(f.fz[fzi + (long long)g.n1 * g.n0]);
+    }
+    return dg;
+}
+
+// Global warp id and lane for row kernels.
+__device__ __forceinline__ long long gwarp() {
+    return ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+}
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Every kernel of the library is launched through launch(): it counts launches
+// (reported by aao_rk_launch_count) and forwards to <<<grid, block, shmem, stream>>>.
+extern long long g_launches;
+template <class... KArgs, class... Args>
+inline void launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t shmem, cudaStream_t st, Args... args) {
+    ++g_launches;
+    k<<<grid, block, shmem, st>>>(args...);
+}
+
+inline unsigned int blocks_for_rows(long long rows) {
+    long long b = (rows + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    return (unsigned int)(b < 1 ? 1 : b);
+}
+
+// ---------------------------------------------------------------------------
+// Error state (thread-local last error text)
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+const char* get_error();
+
+#define AAO_CUDA_TRY(expr)                                                            \
+    do {                                                                              \
+        cudaError_t _e = (expr);                                                      \
+        if (_e != cudaSuccess) {                                                      \
+            ::aao::set_error(std::string(#expr " failed: ") + cudaGetErrorString(_e)); \
+            return _e == cudaErrorMemoryAllocation ? AAO_ERR_OOM : AAO_ERR_CUDA;      \
+        }                                                                             \
+    } while (0)
+
+#define AAO_TRY(expr)                          \
+    do {                                       \
+        aao_status _s = (expr);                \
+        if (_s != AAO_OK) return _s;           \
+    } while (0)
+
+#define AAO_LAUNCH_CHECK()                                                          \
+    do {                                                                            \
+        cudaError_t _e = cudaGetLastError();                                        \
+        if (_e != cudaSuccess) {                                                    \
+            ::aao::set_error(std::string("kernel launch failed: ") + cudaGetErrorString(_e)); \
+            return AAO_ERR_CUDA;                                                    \
+        }                                                                           \
+    } while (0)
+
+}  // namespace aao

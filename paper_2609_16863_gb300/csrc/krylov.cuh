@@ -1,0 +1,513 @@
+// Row kernels of the Krylov and stage pieces:
+//   * batched reductions (norms, modified Gram--Schmidt steps) with a
+//     deterministic last-block finish, one result per batch item;
+//   * Givens update and Hessenberg back-substitution per batch item;
+//   * basis writes, Z y combinations;
+//   * Theta_hat application (Eq. discretized_system_stages) and the Rana
+//     stage-sweep right-hand side;
+//   * the Schur forward / backward substitution steps (Eq. AppSchur);
+//   * the FP64 all-at-once matvec and its transpose (Eq. system_all_at_once_RK).
+#pragma once
+
+#include "common.cuh"
+
+namespace aao {
+
+// ---------------------------------------------------------------------------
+// Reductions: grid (nchunk, B), block kBlock.  Every batch item b spans `rows`
+// rows of n0 values; block x of item b takes rows x*8+w, x*8+w + nchunk*8, ...
+// Partial sums are double; the last block of item b (arrival counter) adds
+// them in chunk order, so the result does not depend on scheduling.
+// ---------------------------------------------------------------------------
+struct Red {
+    double* partials;     // B * nchunk
+    unsigned int* count;  // B, zero between launches
+    int nchunk;
+};
+
+__device__ __forceinline__ void block_finish(double v, int b, const Red& red, double* out, int do_sqrt) {
+    __shared__ double sh[kWarpsPerBlock];
+    __shared__ bool last;
+    v = warp_sum(v);
+    int w = threadIdx.x >> 5;
+    if (lane_id() == 0) sh[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kWarpsPerBlock; ++i) t += sh[i];
+        red.partials[(long long)b * red.nchunk + blockIdx.x] = t;
+        __threadfence();
+        unsigned int prev = atomicAdd(&red.count[b], 1u);
+        last = (prev == (unsigned int)red.nchunk - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double t = 0.0;
+        const volatile double* p = red.partials + (long long)b * red.nchunk;
+        for (int i = 0; i < red.nchunk; ++i) t += p[i];
+        *out = do_sqrt ? sqrt(t) : t;
+        red.count[b] = 0;
+    }
+}
+
+// ||src_b|| for an unscaled source (double or float), rows of n0.
+template <class SR>
+__global__ void __launch_bounds__(kBlock) k_norm(int n0, long long rows, int B, const int* active,
+                                                 const SR* src, long long bs, Red red, double* out,
+                                                 long long ostride) {
+    int b = blockIdx.y;
+    if (active && !active[b]) return;
+    const SR* x = src + (long long)b * bs;
+    int w = threadIdx.x >> 5, lane = lane_id();
+    SR acc = SR(0);
+    for (long long r = (long long)blockIdx.x * kWarpsPerBlock + w; r < rows; r += (long long)red.nchunk * kWarpsPerBlock)
+        for (int c = lane; c < n0; c += kWarp) {
+            SR v = x[r * n0 + c];
+            acc += v * v;
+        }
+    block_finish((double)acc, b, red, out + (long long)b * ostride, 1);
+}
+
+// One modified Gram--Schmidt step on w (arithmetic type A, unscaled):
+//   if Vp: w -= hp[b] * Vp;   then   out[b] = Vn . w   (or ||w|| when Vn is null).
+template <class SV, class A>
+__global__ void __launch_bounds__(kBlock) k_mgs(int n0, long long rows, int B, const int* active, A* wv,
+                                                long long wbs, Vec<SV> Vp, const double* hp, Vec<SV> Vn,
+                                                long long hstride, Red red, double* out) {
+    int b = blockIdx.y;
+    if (active && !active[b]) return;
+    A* w = wv + (long long)b * wbs;
+    const bool upd = Vp.d != nullptr, dot = Vn.d != nullptr;
+    View<SV> vp = upd ? view_of(Vp, b, 0, n0) : View<SV>{nullptr, nullptr, n0};
+    View<SV> vn = dot ? view_of(Vn, b, 0, n0) : View<SV>{nullptr, nullptr, n0};
+    A h = upd ? (A)hp[(long long)b * hstride] : A(0);
+    int wi = threadIdx.x >> 5, lane = lane_id();
+    A acc = A(0);
+    for (long long r = (long long)blockIdx.x * kWarpsPerBlock + wi; r < rows; r += (long long)red.nchunk * kWarpsPerBlock)
+        for (int c = lane; c < n0; c += kWarp) {
+            long long i = r * n0 + c;
+            A x = w[i];
+            if (upd) {
+                x -= h * vp.at(r, c);
+                w[i] = x;
+            }
+            acc += dot ? vn.at(r, c) * x : x * x;
+        }
+    block_finish((double)acc, b, red, out + (long long)b * hstride, dot ? 0 : 1);
+}
+
+// out_b = src_b / denom[b * dstride]  (row store, any storage); inactive items skipped.
+template <class SO, class SR>
+__global__ void __launch_bounds__(kBlock) k_scale_store(int n0, long long rows, int B, const int* active,
+                                                        const SR* src, long long sbs, const double* denom,
+                                                        long long dstride, Vec<SO> out) {
+    long long w = gwarp();
+    if (w >= (long long)B * rows) return;
+    int b = (int)(w / rows);
+    long long row = w % rows;
+    if (active && !active[b]) return;
+    using A = typename PT<SO>::A;
+    const SR* x = src + (long long)b * sbs + row * n0;
+    A inv = denom ? A(1.0 / denom[(long long)b * dstride]) : A(1);
+    SO* o; float* osc;
+    row_store_ptrs(out, b, 0, row, n0, o, osc);
+    row_store<SO>(o, osc, n0, lane_id(), [&](int c) -> A { return A(x[c]) * inv; });
+}
+
+// Read a stored vector back into an unscaled array.
+template <class S, class SO>
+__global__ void __launch_bounds__(kBlock) k_load(int n0, long long rows, int B, Vec<S> in, SO* out, long long obs) {
+    long long w = gwarp();
+    if (w >= (long long)B * rows) return;
+    int b = (int)(w / rows);
+    long long row = w % rows;
+    View<S> v = view_of(in, b, 0, n0);
+    SO* o = out + (long long)b * obs + row * n0;
+    for (int c = lane_id(); c < n0; c += kWarp) o[c] = (SO)v.at(row, c);
+}
+
+// ---------------------------------------------------------------------------
+// Givens update of column k of every item's Hessenberg matrix (Algorithm 1's
+// least-squares problem).  H[b] is (kmax+1) x kmax row-major, stride hs.
+// done[b] is set when |g_{k+1}| <= tol*beta_ref[b], h_{k+1,k} == 0 or k == kmax-1.
+// ---------------------------------------------------------------------------
+static __global__ void k_givens(int B, int k, int kmax, double* H, long long hs, double* cs, double* sn, double* g,
+                         const double* beta_ref, double tol, int* active, int* its, int* nonfinite,
+                         double* resid_out) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B || !active[b]) return;
+    double* h = H + (long long)b * hs;
+    double* c_ = cs + (long long)b * kmax;
+    double* s_ = sn + (long long)b * kmax;
+    double* g_ = g + (long long)b * (kmax + 1);
+    for (int i = 0; i < k; ++i) {
+        double a = h[i * kmax + k], bb = h[(i + 1) * kmax + k];
+        h[i * kmax + k] = c_[i] * a + s_[i] * bb;
+        h[(i + 1) * kmax + k] = -s_[i] * a + c_[i] * bb;
+    }
+    double a = h[k * kmax + k], hk1 = h[(k + 1) * kmax + k];
+    double den = hypot(a, hk1);
+    double cc = 1.0, ss = 0.0;
+    if (den != 0.0) {
+        cc = a / den;
+        ss = hk1 / den;
+    }
+    c_[k] = cc;
+    s_[k] = ss;
+    h[k * kmax + k] = den;
+    g_[k + 1] = -ss * g_[k];
+    g_[k] = cc * g_[k];
+    // keep the unrotated h_{k+1,k} for the basis write (denominator)
+    h[(k + 1) * kmax + k] = hk1;
+    double res = fabs(g_[k + 1]);
+    if (resid_out) resid_out[b] = res;
+    its[b] = k + 1;
+    if (!isfinite(res) || !isfinite(den)) {
+        atomicExch(nonfinite, 1);
+        active[b] = 0;
+        return;
+    }
+    if (res <= tol * beta_ref[b] || hk1 == 0.0 || k == kmax - 1) active[b] = 0;
+}
+
+// Start of a batched inner solve: items with beta == 0 are done at once (z = 0).
+static __global__ void k_inner_init(int B, int kmax, const double* beta, int* active, int* its, double* g, int* nonfinite) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double bt = beta[b];
+    if (!isfinite(bt)) atomicExch(nonfinite, 1);
+    active[b] = (bt > 0.0 && isfinite(bt)) ? 1 : 0;
+    its[b] = 0;
+    for (int i = 0; i <= kmax; ++i) g[(long long)b * (kmax + 1) + i] = i == 0 ? bt : 0.0;
+}
+
+static __global__ void k_count_its(int B, const int* its, long long* count) {
+    __shared__ long long sh[128];
+    long long t = 0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) t += its[b];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long a = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) a += sh[i];
+        *count += a;
+    }
+}
+
+// y = R^{-1} g (R the rotated upper triangle, its[b] columns), per item.
+static __global__ void k_hess_solve(int B, int kmax, const double* H, long long hs, const double* g, const int* its,
+                             double* y, int* breakdown) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double* h = H + (long long)b * hs;
+    const double* g_ = g + (long long)b * (kmax + 1);
+    double* y_ = y + (long long)b * kmax;
+    int m = its[b];
+    for (int i = m - 1; i >= 0; --i) {
+        double t = g_[i];
+        for (int j = i + 1; j < m; ++j) t -= h[i * kmax + j] * y_[j];
+        double d = h[i * kmax + i];
+        if (d == 0.0) {
+            atomicExch(breakdown, 1);
+            y_[i] = 0.0;
+        } else {
+            y_[i] = t / d;
+        }
+    }
+    for (int i = m; i < kmax; ++i) y_[i] = 0.0;
+}
+
+// out_b (+)= sum_{k < its[b]} y[b][k] Z_k,b ; Z_k at Z0 shifted by k*zstride elements.
+template <class SZ, class SO>
+__global__ void __launch_bounds__(kBlock) k_combine(int n0, long long rows, int B, Vec<SZ> Z0, long long zstride,
+                                                    const double* y, int kmax, const int* its, SO* out,
+                                                    long long obs, int accumulate) {
+    long long w = gwarp();
+    if (w >= (long long)B * rows) return;
+    int b = (int)(w / rows);
+    long long row = w % rows;
+    using A = typename PT<SZ>::A;
+    int m = its ? its[b] : kmax;
+    A yk[kMaxRestart];
+    for (int k = 0; k < m; ++k) yk[k] = (A)y[(long long)b * kmax + k];
+    SO* o = out + (long long)b * obs + row * n0;
+    for (int c = lane_id(); c < n0; c += kWarp) {
+        A acc = accumulate ? A(o[c]) : A(0);
+        for (int k = 0; k < m; ++k) {
+            Vec<SZ> Zk = Z0;
+            Zk.d += k * zstride;
+            if constexpr (PT<SZ>::scaled) Zk.sc += (k * zstride) / n0;
+            View<SZ> z = view_of(Zk, b, 0, n0);
+            acc += yk[k] * z.at(row, c);
+        }
+        o[c] = (SO)acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Theta_hat z (Eq. discretized_system_stages with M = I):
+//   w_i = z_i + tau sum_j coef[i*s + j] K z_j,  coef = A_RK (or A_RK^T).
+// One warp per (item, spatial row); every stage of the row at once.
+// ---------------------------------------------------------------------------
+template <class SZ, class A>
+__global__ void __launch_bounds__(kBlock) k_theta(Geo g, int B, const int* active, Vec<SZ> Z, A* wv,
+                                                  long long wbs, int s, const double* coef, A tau,
+                                                  Faces<A> faces) {
+    long long w = gwarp();
+    if (w >= (long long)B * g.R) return;
+    int b = (int)(w / g.R);
+    long long row = w % g.R;
+    if (active && !active[b]) return;
+    int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    A cf[kMaxS * kMaxS];
+    for (int i = 0; i < s * s; ++i) cf[i] = tau * (A)coef[i];
+    View<SZ> zs[kMaxS];
+    for (int i = 0; i < s; ++i) zs[i] = view_of(Z, b, (long long)i * g.nx, g.n0);
+    A* out = wv + (long long)b * wbs + row * g.n0;
+    for (int c = lane_id(); c < g.n0; c += kWarp) {
+        A kz[kMaxS];
+        for (int i = 0; i < s; ++i) kz[i] = (A)fd_K(zs[i], g, faces, row, j, k, c);
+        for (int i = 0; i < s; ++i) {
+            A acc = (A)zs[i].at(row, c);
+            for (int jj = 0; jj < s; ++jj) acc += cf[i * s + jj] * kz[jj];
+            out[(long long)i * g.nx + c] = acc;
+        }
+    }
+}
+
+// Rana stage-sweep right-hand side: out = V_stage - tau sum_j coef[j] K Z_j.
+template <class SV, class SZ>
+__global__ void __launch_bounds__(kBlock) k_rana_rhs(Geo g, int B, const int* active, Vec<SV> V, int stage,
+                                                     Vec<SZ> Z, int s, const double* coef,
+                                                     typename PT<SZ>::A tau, Faces<typename PT<SZ>::A> faces,
+                                                     Vec<SZ> out) {
+    using A = typename PT<SZ>::A;
+    long long w = gwarp();
+    if (w >= (long long)B * g.R) return;
+    int b = (int)(w / g.R);
+    long long row = w % g.R;
+    if (active && !active[b]) return;
+    int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    View<SV> v = view_of(V, b, (long long)stage * g.nx, g.n0);
+    A cf[kMaxS];
+    View<SZ> zs[kMaxS];
+    int nz = 0;
+    for (int jj = 0; jj < s; ++jj)
+        if (coef[jj] != 0.0) {
+            cf[nz] = tau * (A)coef[jj];
+            zs[nz] = view_of(Z, b, (long long)jj * g.nx, g.n0);
+            ++nz;
+        }
+    SZ* o; float* osc;
+    row_store_ptrs(out, b, 0, row, g.n0, o, osc);
+    row_store<SZ>(o, osc, g.n0, lane_id(), [&](int c) -> A {
+        A acc = (A)v.at(row, c);
+        for (int q = 0; q < nz; ++q) acc -= cf[q] * (A)fd_K(zs[q], g, faces, row, j, k, c);
+        return acc;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Schur substitution pieces (Eq. AppSchur, FD: M = I).  The recurrence runs
+// in arithmetic type A; z_v lives in the FP64 output vector.
+// ---------------------------------------------------------------------------
+// w_0 = r_{v,0}; w_{n+1} = r_{v,n+1} + tau sum_i b_i zV_{n,i};  z_{v,0} = w_0.
+template <class A>
+__global__ void k_schur_g(long long nx, int nt, int s, const double* r, const double* zV, const double* bw,
+                          double tau, A* wbuf, double* zv0) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long tot = (long long)(nt + 1) * nx;
+    if (i >= tot) return;
+    long long n = i / nx, p = i % nx;
+    A v;
+    if (n == 0) {
+        v = (A)r[p];
+        zv0[p] = (double)v;
+    } else {
+        A acc = A(0);
+        const double* z = zV + (n - 1) * s * nx + p;
+        for (int q = 0; q < s; ++q) acc += (A)bw[q] * (A)z[(long long)q * nx];
+        v = (A)r[i] + (A)tau * acc;
+    }
+    wbuf[i] = v;
+}
+
+// t_i = K z_{v,n} for every stage i (the e (x) K z_{v,n} right-hand side).
+template <class A>
+__global__ void __launch_bounds__(kBlock) k_schur_rhs(Geo g, int s, const double* zvn, A* t, Faces<A> faces) {
+    long long row = gwarp();
+    if (row >= g.R) return;
+    int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    View<double> z{zvn, nullptr, g.n0};
+    for (int c = lane_id(); c < g.n0; c += kWarp) {
+        A v = (A)fd_K(z, g, faces, row, j, k, c);
+        for (int i = 0; i < s; ++i) t[(long long)i * g.nx + row * g.n0 + c] = v;
+    }
+}
+
+// z_{v,n+1} = w_{n+1} + z_{v,n} - tau sum_i b_i q_i,  q = sum_k y_k Z_k (item 0).
+template <class SZ, class A>
+__global__ void __launch_bounds__(kBlock) k_schur_update(Geo g, int s, const A* wn1, const double* zvn,
+                                                         Vec<SZ> Z0, long long zstride, const double* y,
+                                                         int kmax, const int* its, const double* bw,
+                                                         double tau, double* zvn1) {
+    long long row = gwarp();
+    if (row >= g.R) return;
+    int m = its[0];
+    A coef[kMaxInner * kMaxS];
+    for (int k = 0; k < m; ++k)
+        for (int i = 0; i < s; ++i) coef[k * s + i] = (A)(tau * bw[i] * y[k]);
+    for (int c = lane_id(); c < g.n0; c += kWarp) {
+        long long p = row * g.n0 + c;
+        A acc = wn1[p] + (A)zvn[p];
+        for (int k = 0; k < m; ++k) {
+            Vec<SZ> Zk = Z0;
+            Zk.d += k * zstride;
+            if constexpr (PT<SZ>::scaled) Zk.sc += (k * zstride) / g.n0;
+            for (int i = 0; i < s; ++i) {
+                View<SZ> z = view_of(Zk, 0, (long long)i * g.nx, g.n0);
+                acc -= coef[k * s + i] * z.at(row, c);
+            }
+        }
+        zvn1[p] = (double)acc;
+    }
+}
+
+// Transposed substitution: t_i = b_i u_{n+1}.
+template <class A>
+__global__ void k_schurT_rhs(long long nx, int s, const double* un1, const double* bw, A* t) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)s * nx) return;
+    int q = (int)(i / nx);
+    t[i] = (A)bw[q] * (A)un1[i % nx];
+}
+
+// u_n = r_{v,n} + u_{n+1} - tau sum_i K q_i   (q flat, s*nx, type A).
+template <class A>
+__global__ void __launch_bounds__(kBlock) k_schurT_update(Geo g, int s, const double* rvn, const double* un1,
+                                                          const A* q, double tau, Faces<A> faces, double* un) {
+    long long row = gwarp();
+    if (row >= g.R) return;
+    int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    View<A> qs[kMaxS];
+    for (int i = 0; i < s; ++i) qs[i] = View<A>{q + (long long)i * g.nx, nullptr, g.n0};
+    for (int c = lane_id(); c < g.n0; c += kWarp) {
+        long long p = row * g.n0 + c;
+        A acc = A(0);
+        for (int i = 0; i < s; ++i) acc += (A)fd_K(qs[i], g, faces, row, j, k, c);
+        un[p] = (double)((A)rvn[p] + (A)un1[p] - (A)tau * acc);
+    }
+}
+
+// t_{n,i} = r_{V,n,i} + tau b_i z_{v,n+1}  (all n at once, type A).
+template <class A>
+__global__ void k_schurT_vrhs(long long nx, int nt, int s, const double* rV, const double* zv, const double* bw,
+                              double tau, A* t) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long tot = (long long)nt * s * nx;
+    if (i >= tot) return;
+    long long n = i / ((long long)s * nx);
+    int q = (int)((i / nx) % s);
+    long long p = i % nx;
+    t[i] = (A)rV[i] + (A)tau * (A)bw[q] * (A)zv[(n + 1) * nx + p];
+}
+
+template <class SI, class SO>
+__global__ void k_convert(const SI* in, SO* out, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (SO)in[i];
+}
+
+// ---------------------------------------------------------------------------
+// FP64 all-at-once matvec (FD, M = I), one warp per (time block n, row):
+//   y_{v,0}   = v_0
+//   y_{v,n+1} = v_{n+1} - v_n - tau sum_i b_i V_{n,i}
+//   y_{V,n,i} = V_{n,i} + K v_n + tau sum_j a_ij K V_{n,j}
+// and its transpose
+//   y_{v,n}   = l_{v,n} - l_{v,n+1} + sum_i K l_{V,n,i}   (n < nt),  y_{v,nt} = l_{v,nt}
+//   y_{V,n,i} = l_{V,n,i} - tau b_i l_{v,n+1} + tau sum_j a_ji K l_{V,n,j}.
+// rhs != nullptr gives y = rhs - (A x).  Warps with n == nt handle block v_0 / v_nt.
+// ---------------------------------------------------------------------------
+struct Tab {
+    int s;
+    double A[kMaxS * kMaxS];
+    double b[kMaxS];
+};
+
+static __global__ void __launch_bounds__(kBlock) k_matvec(Geo g, int nt, Tab tab, double tau, Faces<double> faces,
+                                                   const double* x, double* y, const double* rhs, int transpose) {
+    long long w = gwarp();
+    if (w >= (long long)(nt + 1) * g.R) return;
+    int n = (int)(w / g.R);
+    long long row = w % g.R;
+    int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    const int s = tab.s;
+    const long long nx = g.nx;
+    const long long voff = (long long)(nt + 1) * nx;
+    const int lane = lane_id();
+    if (n == nt) {   // y_{v,0} (forward) or y_{v,nt} (transpose)
+        long long base = (transpose ? (long long)nt * nx : 0) + row * g.n0;
+        for (int c = lane; c < g.n0; c += kWarp) {
+            double v = x[base + c];
+            y[base + c] = rhs ? rhs[base + c] - v : v;
+        }
+        return;
+    }
+    View<double> vn{x + (long long)n * nx, nullptr, g.n0};
+    View<double> Vs[kMaxS];
+    for (int i = 0; i < s; ++i) Vs[i] = View<double>{x + voff + ((long long)n * s + i) * nx, nullptr, g.n0};
+    for (int c = lane; c < g.n0; c += kWarp) {
+        long long p = row * g.n0 + c;
+        double KV[kMaxS];
+        for (int i = 0; i < s; ++i) KV[i] = fd_K(Vs[i], g, faces, row, j, k, c);
+        if (!transpose) {
+            double Kv = fd_K(vn, g, faces, row, j, k, c);
+            double acc = x[(long long)(n + 1) * nx + p] - x[(long long)n * nx + p];
+            for (int i = 0; i < s; ++i) acc -= tau * tab.b[i] * Vs[i].at(row, c);
+            long long yi = (long long)(n + 1) * nx + p;
+            y[yi] = rhs ? rhs[yi] - acc : acc;
+            for (int i = 0; i < s; ++i) {
+                double a = Vs[i].at(row, c) + Kv;
+                for (int q = 0; q < s; ++q) a += tau * tab.A[i * s + q] * KV[q];
+                long long yv = voff + ((long long)n * s + i) * nx + p;
+                y[yv] = rhs ? rhs[yv] - a : a;
+            }
+        } else {
+            double ln1 = x[(long long)(n + 1) * nx + p];
+            double acc = x[(long long)n * nx + p] - ln1;
+            for (int i = 0; i < s; ++i) acc += KV[i];
+            long long yi = (long long)n * nx + p;
+            y[yi] = rhs ? rhs[yi] - acc : acc;
+            for (int i = 0; i < s; ++i) {
+                double a = Vs[i].at(row, c) - tau * tab.b[i] * ln1;
+                for (int q = 0; q < s; ++q) a += tau * tab.A[q * s + i] * KV[q];
+                long long yv = voff + ((long long)n * s + i) * nx + p;
+                y[yv] = rhs ? rhs[yv] - a : a;
+            }
+        }
+    }
+}
+
+// rhs = [u0 ; 0 ; f_{n,i}]  (FD, M = I)
+static __global__ void k_rhs(long long nx, int nt, int s, const double* f, int f_time_dep, const double* u0, double* out) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nv = (long long)(nt + 1) * nx;
+    long long tot = nv + (long long)nt * s * nx;
+    if (i >= tot) return;
+    if (i < nx) out[i] = u0[i];
+    else if (i < nv) out[i] = 0.0;
+    else out[i] = f_time_dep ? f[i - nv] : f[(i - nv) % nx];
+}
+
+// grad_f = sum_{n,i} lambda_{V,n,i}  (FD, M = I)
+static __global__ void k_grad_f(long long nx, int nt, int s, const double* lam, double* gf) {
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nx) return;
+    const double* lV = lam + (long long)(nt + 1) * nx;
+    double acc = 0.0;
+    for (long long q = 0; q < (long long)nt * s; ++q) acc += lV[q * nx + p];
+    gf[p] = acc;
+}
+
+}  // namespace aao

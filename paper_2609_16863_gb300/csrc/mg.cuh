@@ -1,0 +1,441 @@
+// Geometric Galerkin multigrid for the shifted operators M + c K (Sec. 5:
+// "(M + cK)^{-1} by 3 V-cycles"; the paper's closed AMG is replaced by a
+// geometric V-cycle with a fixed definition):
+//   coarse points = even fine indices (1-based), N_c = N / 2 per axis;
+//   1D interpolation: injection at coarse points, average of the two
+//   neighbours at odd points (a Dirichlet neighbour counts 0); P = tensor
+//   product, R = P^T, A_c = P^T A P stored as a 3^d-point stencil per point;
+//   damped-Jacobi smoothing; dense exact solve at the coarsest level.
+// All kernels are row kernels: one warp per (batch item, grid row), lanes
+// along x, so a row's per-row scale (16-bit storage) is one warp reduction.
+#pragma once
+
+#include "common.cuh"
+
+namespace aao {
+
+// Operator of one level as the kernels see it, arithmetic type A.
+template <class S> struct LevelOp {
+    using A = typename PT<S>::A;
+    Geo g;
+    int fine = 1;            // 1: matrix-free sigma*u + c*K u; 0: stored stencil
+    A sigma = A(1), c = A(0);
+    Faces<A> faces;          // fine level, variable kappa (nullptr = kappa 1)
+    const S* sten = nullptr; // coarse: ncoef*nx, component-major
+    const float* sten_sc = nullptr;  // coarse, scaled types: one scale per component
+    int ncoef = 9;
+};
+
+template <class S>
+__device__ __forceinline__ typename PT<S>::A sten_coef(const LevelOp<S>& op, int q, long long p) {
+    typename PT<S>::A v = PT<S>::ld(op.sten[(long long)q * op.g.nx + p]);
+    if constexpr (PT<S>::scaled) v *= op.sten_sc[q];
+    return v;
+}
+
+// (A u)_P and the diagonal a_PP at column c of row (j,k).
+template <class S, class SU>
+__device__ __forceinline__ void level_apply(const LevelOp<S>& op, const View<SU>& u, long long row, int j,
+                                            int k, int c, typename PT<S>::A& Au,
+                                            typename PT<S>::A& diag) {
+    using A = typename PT<S>::A;
+    const Geo& g = op.g;
+    if (op.fine) {
+        Au = op.sigma * A(u.at(row, c)) + op.c * A(fd_K(u, g, op.faces, row, j, k, c));
+        diag = op.sigma + op.c * fd_K_diag<A>(g, op.faces, row, j, k, c);
+        return;
+    }
+    const long long p = row * g.n0 + c;
+    A acc = A(0);
+    const int zlo = g.d == 3 ? -1 : 0, zhi = g.d == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+        int kk = k + dz;
+        if (kk < 0 || kk >= g.n2) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int jj = j + dy;
+            if (jj < 0 || jj >= g.n1) continue;
+            long long rr = row + dy + (long long)dz * g.n1;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                int cc = c + dx;
+                if (cc < 0 || cc >= g.n0) continue;
+                int q = (dx + 1) + 3 * (dy + 1) + (g.d == 3 ? 9 * (dz + 1) : 0);
+                acc += sten_coef(op, q, p) * A(u.at(rr, cc));
+            }
+        }
+    }
+    Au = acc;
+    diag = sten_coef(op, g.d == 3 ? 13 : 4, p);
+}
+
+// x_out = x_in + omega D^{-1} (b - A x_in); x_in.d == nullptr means x_in = 0.
+template <class S>
+__global__ void __launch_bounds__(kBlock) k_smooth(LevelOp<S> op, int B, const int* active, Vec<S> xin,
+                                                   Vec<S> bv, Vec<S> xout, typename PT<S>::A omega) {
+    using A = typename PT<S>::A;
+    const Geo g = op.g;
+    long long w = gwarp();
+    if (w >= (long long)B * g.R) return;
+    int b = (int)(w / g.R);
+    long long row = w % g.R;
+    if (active && !active[b]) return;
+    int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    int lane = lane_id();
+    View<S> bb = view_of(bv, b, 0, g.n0);
+    S* out; float* osc;
+    row_store_ptrs(xout, b, 0, row, g.n0, out, osc);
+    if (xin.d == nullptr) {
+        row_store<S>(out, osc, g.n0, lane, [&](int c) -> A {
+            A Au, dg;
+            // diagonal only: A x = 0
+            if (op.fine) {
+                dg = op.sigma + op.c * fd_K_diag<A>(g, op.faces, row, j, k, c);
+            } else {
+                dg = sten_coef(op, g.d == 3 ? 13 : 4, row * g.n0 + c);
+            }
+            (void)Au;
+            return omega * bb.at(row, c) / dg;
+        });
+    } else {
+        View<S> xx = view_of(xin, b, 0, g.n0);
+        row_store<S>(out, osc, g.n0, lane, [&](int c) -> A {
+            A Au, dg;
+            level_apply(op, xx, row, j, k, c, Au, dg);
+            return xx.at(row, c) + omega * (bb.at(row, c) - Au) / dg;
+        });
+    }
+}
+
+// r = b - A x
+template <class S>
+__global__ void __launch_bounds__(kBlock) k_residual(LevelOp<S> op, int B, const int* active, Vec<S> xv,
+                                                     Vec<S> bv, Vec<S> rv) {
+    using A = typename PT<S>::A;
+    const Geo g = op.g;
+    long long w = gwarp();
+    if (w >= (long long)B * g.R) return;
+    int b = (int)(w / g.R);
+    long long row = w % g.R;
+    if (active && !active[b]) return;
+    int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    View<S> xx = view_of(xv, b, 0, g.n0);
+    View<S> bb = view_of(bv, b, 0, g.n0);
+    S* out; float* osc;
+    row_store_ptrs(rv, b, 0, row, g.n0, out, osc);
+    row_store<S>(out, osc, g.n0, lane_id(), [&](int c) -> A {
+        A Au, dg;
+        level_apply(op, xx, row, j, k, c, Au, dg);
+        return bb.at(row, c) - Au;
+    });
+}
+
+// bc = P^T r  (coarse row kernel)
+template <class S>
+__global__ void __launch_bounds__(kBlock) k_restrict(Geo gf, Geo gc, int B, const int* active, Vec<S> rv,
+                                                     Vec<S> bcv) {
+    using A = typename PT<S>::A;
+    long long w = gwarp();
+    if (w >= (long long)B * gc.R) return;
+    int b = (int)(w / gc.R);
+    long long row = w % gc.R;
+    if (active && !active[b]) return;
+    int J = (int)(row % gc.n1), Kc = (int)(row / gc.n1);
+    View<S> rr = view_of(rv, b, 0, gf.n0);
+    S* out; float* osc;
+    row_store_ptrs(bcv, b, 0, row, gc.n0, out, osc);
+    row_store<S>(out, osc, gc.n0, lane_id(), [&](int I) -> A {
+        A acc = A(0);
+        const int zlo = gf.d == 3 ? -1 : 0, zhi = gf.d == 3 ? 1 : 0;
+        for (int dz = zlo; dz <= zhi; ++dz) {
+            int fk = gf.d == 3 ? 2 * Kc + 1 + dz : 0;
+            if (fk < 0 || fk >= gf.n2) continue;
+            A wz = dz == 0 ? A(1) : A(0.5);
+            for (int dy = -1; dy <= 1; ++dy) {
+                int fj = 2 * J + 1 + dy;
+                if (fj < 0 || fj >= gf.n1) continue;
+                A wy = dy == 0 ? A(1) : A(0.5);
+                long long frow = fj + (long long)gf.n1 * fk;
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int fi = 2 * I + 1 + dx;
+                    if (fi < 0 || fi >= gf.n0) continue;
+                    A wx = dx == 0 ? A(1) : A(0.5);
+                    acc += wx * wy * wz * rr.at(frow, fi);
+                }
+            }
+        }
+        return acc;
+    });
+}
+
+// 1D interpolation stencil of fine 0-based index F: up to two coarse indices.
+__device__ __forceinline__ int interp_1d(int F, int nc, int* J, float* wt) {
+    int g = F + 1;  // 1-based
+    if ((g & 1) == 0) {
+        J[0] = g / 2 - 1;
+        wt[0] = 1.f;
+        return 1;
+    }
+    int m = 0;
+    int j1 = (g - 1) / 2 - 1, j2 = (g + 1) / 2 - 1;
+    if (j1 >= 0 && j1 < nc) { J[m] = j1; wt[m] = 0.5f; ++m; }
+    if (j2 >= 0 && j2 < nc) { J[m] = j2; wt[m] = 0.5f; ++m; }
+    return m;
+}
+
+// x_out = x_in + P xc  (fine row kernel); x_in.d == nullptr means 0.
+template <class S>
+__global__ void __launch_bounds__(kBlock) k_prolong_add(Geo gf, Geo gc, int B, const int* active, Vec<S> xcv,
+                                                        Vec<S> xin, Vec<S> xout) {
+    using A = typename PT<S>::A;
+    long long w = gwarp();
+    if (w >= (long long)B * gf.R) return;
+    int b = (int)(w / gf.R);
+    long long row = w % gf.R;
+    if (active && !active[b]) return;
+    int j = (int)(row % gf.n1), k = (int)(row / gf.n1);
+    View<S> xc = view_of(xcv, b, 0, gc.n0);
+    const bool has_in = xin.d != nullptr;
+    View<S> xi = has_in ? view_of(xin, b, 0, gf.n0) : View<S>{nullptr, nullptr, gf.n0};
+    int Jy[2], Jz[2] = {0, 0};
+    float wy[2], wz[2] = {1.f, 0.f};
+    int my = interp_1d(j, gc.n1, Jy, wy);
+    int mz = gf.d == 3 ? interp_1d(k, gc.n2, Jz, wz) : 1;
+    S* out; float* osc;
+    row_store_ptrs(xout, b, 0, row, gf.n0, out, osc);
+    row_store<S>(out, osc, gf.n0, lane_id(), [&](int c) -> A {
+        int Jx[2];
+        float wx[2];
+        int mx = interp_1d(c, gc.n0, Jx, wx);
+        A acc = has_in ? xi.at(row, c) : A(0);
+        for (int a = 0; a < mz; ++a)
+            for (int bq = 0; bq < my; ++bq) {
+                long long crow = Jy[bq] + (long long)gc.n1 * Jz[a];
+                A wyz = A(wy[bq]) * A(wz[a]);
+                for (int e = 0; e < mx; ++e) acc += wyz * A(wx[e]) * xc.at(crow, Jx[e]);
+            }
+        return acc;
+    });
+}
+
+// x = Dinv b at the coarsest level (Dinv dense, nc x nc, row-major, arithmetic type).
+template <class S>
+__global__ void __launch_bounds__(kBlock) k_coarse_solve(Geo g, int B, const int* active,
+                                                         const typename PT<S>::A* Dinv, Vec<S> bv,
+                                                         Vec<S> xv) {
+    using A = typename PT<S>::A;
+    long long w = gwarp();
+    if (w >= (long long)B * g.R) return;
+    int b = (int)(w / g.R);
+    long long row = w % g.R;
+    if (active && !active[b]) return;
+    View<S> bb = view_of(bv, b, 0, g.n0);
+    S* out; float* osc;
+    row_store_ptrs(xv, b, 0, row, g.n0, out, osc);
+    const int nc = (int)g.nx;
+    row_store<S>(out, osc, g.n0, lane_id(), [&](int c) -> A {
+        long long p = row * g.n0 + c;
+        A acc = A(0);
+        for (int q = 0; q < nc; ++q) acc += Dinv[p * nc + q] * bb.at(q / g.n0, q % g.n0);
+        return acc;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Set-up (FP64): Galerkin coarse stencil A_c = P^T A P, one thread per coarse
+// point.  The fine operator is either matrix-free FD (sigma I + c K) or a
+// stored FP64 3^d stencil.
+// ---------------------------------------------------------------------------
+struct FineDesc {
+    Geo g;
+    int fine;
+    double sigma, c;
+    Faces<double> faces;
+    const double* sten;
+};
+
+__device__ __forceinline__ int fine_row_entries(const FineDesc& fd, int fi, int fj, int fk, int* gi, int* gj,
+                                                int* gk, double* val) {
+    const Geo& g = fd.g;
+    long long row = fj + (long long)g.n1 * fk;
+    int m = 0;
+    if (fd.fine) {
+        // diagonal and the 2d face neighbours
+        double dg;
+        if (fd.faces.fx == nullptr) {
+            dg = 2 * g.hx2 + 2 * g.hy2 + (g.d == 3 ? 2 * g.hz2 : 0.0);
+        } else {
+            long long fxi = row * (g.n0 + 1) + fi;
+            long long fyi = ((long long)fk * (g.n1 + 1) + fj) * g.n0 + fi;
+            dg = fd.faces.fx[fxi] + fd.faces.fx[fxi + 1] + fd.faces.fy[fyi] + fd.faces.fy[fyi + g.n0];
+            if (g.d == 3) {
+                long long fzi = ((long long)fk * g.n1 + fj) * g.n0 + fi;
+                dg += fd.faces.fz[fzi] + fd.faces.fz[fzi + (long long)g.n1 * g.n0];
+            }
+        }
+        gi[m] = fi; gj[m] = fj; gk[m] = fk; val[m] = fd.sigma + fd.c * dg; ++m;
+        for (int a = 0; a < g.d; ++a)
+            for (int sg = -1; sg <= 1; sg += 2) {
+                int ii = fi + (a == 0 ? sg : 0), jj = fj + (a == 1 ? sg : 0), kk = fk + (a == 2 ? sg : 0);
+                if (ii < 0 || ii >= g.n0 || jj < 0 || jj >= g.n1 || kk < 0 || kk >= g.n2) continue;
+                double face;
+                if (fd.faces.fx == nullptr) {
+                    face = a == 0 ? g.hx2 : (a == 1 ? g.hy2 : g.hz2);
+                } else if (a == 0) {
+                    face = fd.faces.fx[row * (g.n0 + 1) + fi + (sg > 0 ? 1 : 0)];
+                } else if (a == 1) {
+                    face = fd.faces.fy[((long long)fk * (g.n1 + 1) + fj + (sg > 0 ? 1 : 0)) * g.n0 + fi];
+                } else {
+                    face = fd.faces.fz[((long long)(fk + (sg > 0 ? 1 : 0)) * g.n1 + fj) * g.n0 + fi];
+                }
+                gi[m] = ii; gj[m] = jj; gk[m] = kk; val[m] = -fd.c * face; ++m;
+            }
+        return m;
+    }
+    long long p = row * g.n0 + fi;
+    const int zlo = g.d == 3 ? -1 : 0, zhi = g.d == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int ii = fi + dx, jj = fj + dy, kk = fk + dz;
+                if (ii < 0 || ii >= g.n0 || jj < 0 || jj >= g.n1 || kk < 0 || kk >= g.n2) continue;
+                int q = (dx + 1) + 3 * (dy + 1) + (g.d == 3 ? 9 * (dz + 1) : 0);
+                double v = fd.sten[(long long)q * g.nx + p];
+                if (v == 0.0) continue;
+                gi[m] = ii; gj[m] = jj; gk[m] = kk; val[m] = v; ++m;
+            }
+    return m;
+}
+
+static __global__ void k_galerkin(FineDesc fd, Geo gc, double* out) {
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= gc.nx) return;
+    const Geo& gf = fd.g;
+    const int ncoef = gc.d == 3 ? 27 : 9;
+    int I = (int)(p % gc.n0), J = (int)((p / gc.n0) % gc.n1), Kc = (int)(p / ((long long)gc.n0 * gc.n1));
+    double acc[27];
+    for (int q = 0; q < 27; ++q) acc[q] = 0.0;
+    const int zlo = gf.d == 3 ? -1 : 0, zhi = gf.d == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+        int fk = gf.d == 3 ? 2 * Kc + 1 + dz : 0;
+        if (fk < 0 || fk >= gf.n2) continue;
+        double wz = dz == 0 ? 1.0 : 0.5;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int fj = 2 * J + 1 + dy;
+            if (fj < 0 || fj >= gf.n1) continue;
+            double wy = dy == 0 ? 1.0 : 0.5;
+            for (int dx = -1; dx <= 1; ++dx) {
+                int fi = 2 * I + 1 + dx;
+                if (fi < 0 || fi >= gf.n0) continue;
+                double wf = (dx == 0 ? 1.0 : 0.5) * wy * wz;   // P[f, I]
+                int gi[27], gj[27], gk[27];
+                double val[27];
+                int m = fine_row_entries(fd, fi, fj, fk, gi, gj, gk, val);
+                for (int e = 0; e < m; ++e) {
+                    int Jx[2], Jy[2], Jz[2] = {0, 0};
+                    float wx[2], wy2[2], wz2[2] = {1.f, 0.f};
+                    int mx = interp_1d(gi[e], gc.n0, Jx, wx);
+                    int my = interp_1d(gj[e], gc.n1, Jy, wy2);
+                    int mz = gc.d == 3 ? interp_1d(gk[e], gc.n2, Jz, wz2) : 1;
+                    for (int a = 0; a < mz; ++a)
+                        for (int bq = 0; bq < my; ++bq)
+                            for (int cq = 0; cq < mx; ++cq) {
+                                int ox = Jx[cq] - I, oy = Jy[bq] - J, oz = gc.d == 3 ? Jz[a] - Kc : 0;
+                                int q = (ox + 1) + 3 * (oy + 1) + (gc.d == 3 ? 9 * (oz + 1) : 0);
+                                acc[q] += wf * val[e] * (double)wx[cq] * (double)wy2[bq] * (double)wz2[a];
+                            }
+                }
+            }
+        }
+    }
+    for (int q = 0; q < ncoef; ++q) out[(long long)q * gc.nx + p] = acc[q];
+}
+
+// Dense matrix of the coarsest level from its FP64 description (fine or stencil).
+static __global__ void k_dense_level(FineDesc fd, double* Adense) {
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const Geo& g = fd.g;
+    if (p >= g.nx) return;
+    int fi = (int)(p % g.n0), fj = (int)((p / g.n0) % g.n1), fk = (int)(p / ((long long)g.n0 * g.n1));
+    int gi[27], gj[27], gk[27];
+    double val[27];
+    int m = fine_row_entries(fd, fi, fj, fk, gi, gj, gk, val);
+    for (long long q = 0; q < g.nx; ++q) Adense[p * g.nx + q] = 0.0;
+    for (int e = 0; e < m; ++e) {
+        long long q = gi[e] + (long long)g.n0 * (gj[e] + (long long)g.n1 * gk[e]);
+        Adense[p * g.nx + q] += val[e];
+    }
+}
+
+// In-place Gauss--Jordan inverse (SPD input, no pivoting needed), one block.
+static __global__ void k_gauss_jordan(double* A, double* Inv, int n, int* fail) {
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Inv[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        __shared__ double piv;
+        if (threadIdx.x == 0) {
+            piv = A[k * n + k];
+            if (!(piv > 0.0)) *fail = 1;
+        }
+        __syncthreads();
+        double pinv = 1.0 / piv;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            A[k * n + j] *= pinv;
+            Inv[k * n + j] *= pinv;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+            int i = idx / n, j = idx % n;
+            if (i == k) continue;
+            double f = A[i * n + k];
+            if (j != k) A[i * n + j] -= f * A[k * n + j];
+            Inv[i * n + j] -= f * Inv[k * n + j];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            if (i != k) A[i * n + k] = 0.0;
+        __syncthreads();
+    }
+}
+
+// Per-component max |coef| (one block per component) and conversion to S.
+static __global__ void k_stencil_absmax(const double* sten, long long nx, float* cmax) {
+    int q = blockIdx.x;
+    double m = 0.0;
+    for (long long p = threadIdx.x; p < nx; p += blockDim.x) m = fmax(m, fabs(sten[(long long)q * nx + p]));
+    __shared__ double sh[kBlock];
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double mm = sh[0];
+        float sc = 1.f;
+        if (mm > 0.0) {
+            int e;
+            frexp(mm, &e);
+            sc = ldexpf(1.f, e - 14);
+        }
+        cmax[q] = sc;
+    }
+}
+
+template <class S>
+__global__ void k_stencil_convert(const double* sten, long long nx, int ncoef, const float* sc, S* out) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx * ncoef) return;
+    int q = (int)(i / nx);
+    double v = sten[i];
+    if constexpr (PT<S>::scaled) v /= (double)sc[q];
+    out[i] = PT<S>::st((typename PT<S>::A)v);
+}
+
+template <class A>
+__global__ void k_convert_dense(const double* in, A* out, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (A)in[i];
+}
+
+}  // namespace aao

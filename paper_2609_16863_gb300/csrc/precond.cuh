@@ -1,0 +1,532 @@
+// P_tilde of Eq. (AppPrec) in storage precisions SP (Theta_tilde's GMRES basis
+// and the S_tilde recurrence) and SI (Rana's sweep, V-cycles, coarse stencils).
+// Arithmetic is double when SP is double, else float.
+//
+// apply(r):   z_V = Theta_tilde^{-1} r_V, all nt time blocks batched (inner
+//             GMRES, right-preconditioned by P_int);
+//             g_{n+1} = r_{v,n+1} + tau sum_i b_i z_{V,n,i}; w = M^{-1} g (FD: w = g);
+//             z_{v,0} = w_0, z_{v,n+1} = w_{n+1} + z_{v,n} - tau (b^T (x) I)
+//             Theta_tilde^{-1} (e (x) K z_{v,n})    (forward substitution, Eq. AppSchur).
+// apply_T(r): u_nt = r_{v,nt}, u_n = r_{v,n} + u_{n+1} - tau (e^T (x) K)
+//             Theta_tilde^{-T} (b (x) u_{n+1}); z_v = M^{-1} u;
+//             z_V = Theta_tilde^{-T} (r_V + tau (b (x) M) z_{v,n+1}).
+#pragma once
+
+#include <type_traits>
+
+#include "handle.cuh"
+#include "mg.cuh"
+
+namespace aao {
+
+template <class SP, class SI>
+class Precond : public PrecondBase {
+    using A = typename PT<SP>::A;
+    static_assert(std::is_same<typename PT<SP>::A, typename PT<SI>::A>::value,
+                  "P and P_int arithmetic must agree");
+
+    struct Level {
+        Geo g;
+        // per-stage stored stencils (levels >= 1)
+        SI* sten[kMaxS] = {};
+        float* sten_sc[kMaxS] = {};
+        // scratch, Bmax items of nx each
+        Vec<SI> T0, T1, Rr, Bb, X;
+    };
+
+    Handle* h;
+    Arena ar;
+    int Bmax = 0;
+    int L = 0;
+    Level lev[kMaxLevels];
+    A* Dinv[kMaxS] = {};           // dense coarsest inverse per stage
+    Faces<A> facesA;
+    int kin = 0;                   // inner maxit
+    double itol = 0.0;
+    // inner GMRES state
+    Vec<SP> V0;                    // (kin+1) bases, stride vstride elements
+    long long vstride = 0;
+    Vec<SI> Z0;                    // kin bases, stride zstride
+    long long zstride = 0;
+    A* wv = nullptr;               // Bmax * s*nx
+    Vec<SI> mgb;                   // Rana rhs, Bmax * nx
+    double *Hh = nullptr, *csh = nullptr, *snh = nullptr, *gh = nullptr, *yh = nullptr, *betah = nullptr;
+    int *activeh = nullptr, *itsh = nullptr, *nonfin = nullptr, *brk = nullptr;
+    long long* itcount = nullptr;  // running total of inner iterations (device)
+    // Schur state
+    A* wbuf = nullptr;             // (nt+1)*nx
+    A* tbuf = nullptr;             // s*nx
+    A* qbuf = nullptr;             // s*nx
+    A* tV = nullptr;               // nt*s*nx (transposed apply)
+    double* tmp64 = nullptr;       // Bmax*s*nx staging for component entry points
+    cudaEvent_t e0, e1, e2;
+
+    cudaStream_t st() const { return h->stream; }
+
+    template <class S> aao_status alloc_vec(Vec<S>& v, long long items, long long item_len, int n0) {
+        AAO_TRY(ar.alloc(&v.d, (size_t)(items * item_len)));
+        v.bs = item_len;
+        v.sc = nullptr;
+        if (PT<S>::scaled) AAO_TRY(ar.alloc(&v.sc, (size_t)(items * item_len / n0)));
+        return AAO_OK;
+    }
+
+  public:
+    explicit Precond(Handle* hh) : h(hh) {}
+    ~Precond() override { release(); }
+
+    void release() override {
+        ar.release();
+    }
+
+    aao_status setup() override {
+        const Geo& g0 = h->g;
+        const int s = h->s;
+        if (PT<SI>::scaled || PT<SP>::scaled) {
+            if (g0.n0 > kMaxRowLen) {
+                set_error("16-bit storage needs n[0] <= 512");
+                return AAO_ERR_ARG;
+            }
+        }
+        Bmax = h->nt;
+        kin = h->opt.inner_maxit;
+        itol = h->opt.inner_tol;
+        // ---- levels
+        L = 0;
+        Geo g = g0;
+        while (true) {
+            lev[L].g = g;
+            ++L;
+            bool more = g.n0 / 2 >= 2 && g.n1 / 2 >= 2 && (g.d == 2 || g.n2 / 2 >= 2);
+            if (!more || L == kMaxLevels) break;
+            Geo c = g;
+            c.n0 = g.n0 / 2;
+            c.n1 = g.n1 / 2;
+            c.n2 = g.d == 3 ? g.n2 / 2 : 1;
+            c.nx = (long long)c.n0 * c.n1 * c.n2;
+            c.R = c.n1 * c.n2;
+            g = c;
+        }
+        if (lev[L - 1].g.nx > kMaxCoarsest) {
+            set_error("coarsest multigrid level too large (anisotropic grid?)");
+            return AAO_ERR_ARG;
+        }
+        // ---- faces in arithmetic precision
+        if (h->has_kappa) {
+            long long nfx = (long long)(g0.n0 + 1) * g0.R;
+            long long nfy = (long long)g0.n0 * (g0.n1 + 1) * g0.n2;
+            long long nfz = g0.d == 3 ? (long long)g0.nx / g0.n2 * (g0.n2 + 1) : 0;
+            A *fx, *fy, *fz = nullptr;
+            AAO_TRY(ar.alloc(&fx, nfx));
+            AAO_TRY(ar.alloc(&fy, nfy));
+            if (nfz) AAO_TRY(ar.alloc(&fz, nfz));
+            launch(k_convert<double, A>, (unsigned)((nfx + 255) / 256), 256, 0, st(), h->faces64.fx, fx, nfx);
+            launch(k_convert<double, A>, (unsigned)((nfy + 255) / 256), 256, 0, st(), h->faces64.fy, fy, nfy);
+            if (nfz) launch(k_convert<double, A>, (unsigned)((nfz + 255) / 256), 256, 0, st(), h->faces64.fz, fz, nfz);
+            AAO_LAUNCH_CHECK();
+            facesA.fx = fx;
+            facesA.fy = fy;
+            facesA.fz = fz;
+        }
+        // ---- Galerkin hierarchy per stage shift c_i = tau d_i
+        const int ncoef = g0.d == 3 ? 27 : 9;
+        double* sten64[kMaxLevels] = {};
+        for (int l = 1; l < L; ++l) AAO_TRY(ar.alloc(&sten64[l], (size_t)(ncoef * lev[l].g.nx)));
+        const Geo& gcst = lev[L - 1].g;
+        const int ncst = (int)gcst.nx;
+        double *dense, *dinv64;
+        int* fail;
+        AAO_TRY(ar.alloc(&dense, (size_t)ncst * ncst));
+        AAO_TRY(ar.alloc(&dinv64, (size_t)ncst * ncst));
+        AAO_TRY(ar.alloc(&fail, 1));
+        AAO_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), st()));
+        for (int i = 0; i < s; ++i) {
+            FineDesc fd;
+            fd.g = g0;
+            fd.fine = 1;
+            fd.sigma = 1.0;
+            fd.c = h->tau * h->D[i];
+            fd.faces = h->faces64;
+            fd.sten = nullptr;
+            for (int l = 1; l < L; ++l) {
+                launch(k_galerkin, (unsigned)((lev[l].g.nx + 127) / 128), 128, 0, st(), fd, lev[l].g, sten64[l]);
+                AAO_LAUNCH_CHECK();
+                // store in SI
+                if constexpr (std::is_same<SI, double>::value) {
+                    SI* keep;
+                    AAO_TRY(ar.alloc(&keep, (size_t)(ncoef * lev[l].g.nx)));
+                    AAO_CUDA_TRY(cudaMemcpyAsync(keep, sten64[l], sizeof(double) * ncoef * lev[l].g.nx,
+                                                 cudaMemcpyDeviceToDevice, st()));
+                    lev[l].sten[i] = keep;
+                } else {
+                    float* sc;
+                    AAO_TRY(ar.alloc(&sc, ncoef));
+                    if (PT<SI>::scaled) {
+                        launch(k_stencil_absmax, ncoef, kBlock, 0, st(), sten64[l], lev[l].g.nx, sc);
+                    } else {
+                        AAO_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(float) * ncoef, st()));
+                    }
+                    SI* out;
+                    AAO_TRY(ar.alloc(&out, (size_t)(ncoef * lev[l].g.nx)));
+                    long long tot = ncoef * lev[l].g.nx;
+                    launch(k_stencil_convert<SI>, (unsigned)((tot + 255) / 256), 256, 0, st(), 
+                        sten64[l], lev[l].g.nx, ncoef, sc, out);
+                    AAO_LAUNCH_CHECK();
+                    lev[l].sten[i] = out;
+                    lev[l].sten_sc[i] = sc;
+                }
+                FineDesc nd;
+                nd.g = lev[l].g;
+                nd.fine = 0;
+                nd.sigma = 0;
+                nd.c = 0;
+                nd.sten = sten64[l];
+                fd = nd;   // level l+1 is the Galerkin product of this level
+            }
+            // coarsest dense inverse from the FP64 description of level L-1
+            FineDesc cd;
+            if (L == 1) {
+                cd.g = g0;
+                cd.fine = 1;
+                cd.sigma = 1.0;
+                cd.c = h->tau * h->D[i];
+                cd.faces = h->faces64;
+                cd.sten = nullptr;
+            } else {
+                cd.g = gcst;
+                cd.fine = 0;
+                cd.sigma = 0;
+                cd.c = 0;
+                cd.sten = sten64[L - 1];
+            }
+            launch(k_dense_level, (unsigned)((ncst + 127) / 128), 128, 0, st(), cd, dense);
+            launch(k_gauss_jordan, 1, 256, 0, st(), dense, dinv64, ncst, fail);
+            AAO_LAUNCH_CHECK();
+            AAO_TRY(ar.alloc(&Dinv[i], (size_t)ncst * ncst));
+            launch(k_convert_dense<A>, (unsigned)(((long long)ncst * ncst + 255) / 256), 256, 0, st(), 
+                dinv64, Dinv[i], (long long)ncst * ncst);
+            AAO_LAUNCH_CHECK();
+        }
+        int hfail = 0;
+        AAO_CUDA_TRY(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st()));
+        AAO_CUDA_TRY(cudaStreamSynchronize(st()));
+        if (hfail) {
+            set_error("coarsest multigrid operator is not positive definite");
+            return AAO_ERR_BREAKDOWN;
+        }
+        // ---- level scratch
+        for (int l = 0; l < L; ++l) {
+            const Geo& gl = lev[l].g;
+            AAO_TRY(alloc_vec(lev[l].T0, Bmax, gl.nx, gl.n0));
+            AAO_TRY(alloc_vec(lev[l].T1, Bmax, gl.nx, gl.n0));
+            AAO_TRY(alloc_vec(lev[l].Rr, Bmax, gl.nx, gl.n0));
+            if (l > 0) {
+                AAO_TRY(alloc_vec(lev[l].Bb, Bmax, gl.nx, gl.n0));
+                AAO_TRY(alloc_vec(lev[l].X, Bmax, gl.nx, gl.n0));
+            }
+        }
+        // ---- inner GMRES state
+        const long long item = (long long)s * g0.nx;
+        vstride = (long long)Bmax * item;
+        zstride = vstride;
+        AAO_TRY(alloc_vec(V0, (long long)(kin + 1) * Bmax, item, g0.n0));
+        V0.bs = item;
+        AAO_TRY(alloc_vec(Z0, (long long)kin * Bmax, item, g0.n0));
+        Z0.bs = item;
+        AAO_TRY(ar.alloc(&wv, (size_t)(Bmax * item)));
+        AAO_TRY(alloc_vec(mgb, Bmax, g0.nx, g0.n0));
+        AAO_TRY(ar.alloc(&Hh, (size_t)Bmax * (kin + 1) * kin));
+        AAO_TRY(ar.alloc(&csh, (size_t)Bmax * kin));
+        AAO_TRY(ar.alloc(&snh, (size_t)Bmax * kin));
+        AAO_TRY(ar.alloc(&gh, (size_t)Bmax * (kin + 1)));
+        AAO_TRY(ar.alloc(&yh, (size_t)Bmax * kin));
+        AAO_TRY(ar.alloc(&betah, (size_t)Bmax));
+        AAO_TRY(ar.alloc(&activeh, (size_t)Bmax));
+        AAO_TRY(ar.alloc(&itsh, (size_t)Bmax));
+        AAO_TRY(ar.alloc(&nonfin, 2));
+        brk = nonfin + 1;
+        AAO_TRY(ar.alloc(&itcount, 1));
+        AAO_CUDA_TRY(cudaMemsetAsync(nonfin, 0, 2 * sizeof(int), st()));
+        AAO_CUDA_TRY(cudaMemsetAsync(itcount, 0, sizeof(long long), st()));
+        // ---- Schur state
+        AAO_TRY(ar.alloc(&wbuf, (size_t)((h->nt + 1) * g0.nx)));
+        AAO_TRY(ar.alloc(&tbuf, (size_t)item));
+        AAO_TRY(ar.alloc(&qbuf, (size_t)item));
+        AAO_TRY(ar.alloc(&tV, (size_t)(h->nt * item)));
+        AAO_TRY(ar.alloc(&tmp64, (size_t)(Bmax * item)));
+        AAO_CUDA_TRY(cudaEventCreate(&e0));
+        AAO_CUDA_TRY(cudaEventCreate(&e1));
+        AAO_CUDA_TRY(cudaEventCreate(&e2));
+        AAO_CUDA_TRY(cudaStreamSynchronize(st()));
+        return AAO_OK;
+    }
+
+    // ---------------------------------------------------------------- MG
+    LevelOp<SI> level_op(int l, int stage) const {
+        LevelOp<SI> op;
+        op.g = lev[l].g;
+        op.ncoef = op.g.d == 3 ? 27 : 9;
+        if (l == 0) {
+            op.fine = 1;
+            op.sigma = A(1);
+            op.c = (A)(h->tau * h->D[stage]);
+            op.faces = facesA;
+        } else {
+            op.fine = 0;
+            op.sten = lev[l].sten[stage];
+            op.sten_sc = lev[l].sten_sc[stage];
+        }
+        return op;
+    }
+
+    template <class S> static Vec<S> shift_vec(Vec<S> v, long long elems, int n0) {
+        v.d += elems;
+        if (PT<S>::scaled) v.sc += elems / n0;
+        return v;
+    }
+
+    // x_out = V-cycle(l) applied to (x_in, b); x_in.d == nullptr: zero guess.
+    aao_status vcycle(int l, int stage, int B, const int* act, Vec<SI> xin, Vec<SI> b, Vec<SI> xout) {
+        const Geo& g = lev[l].g;
+        unsigned nb = blocks_for_rows((long long)B * g.R);
+        if (l == L - 1) {
+            launch(k_coarse_solve<SI>, nb, kBlock, 0, st(), g, B, act, Dinv[stage], b, xout);
+            AAO_LAUNCH_CHECK();
+            return AAO_OK;
+        }
+        LevelOp<SI> op = level_op(l, stage);
+        const A om = (A)h->opt.mg_omega;
+        const int nu1 = h->opt.mg_pre, nu2 = h->opt.mg_post;
+        const int nops = nu1 + 1 + nu2;
+        Vec<SI> cur = xin;
+        int opi = 0;
+        auto dest = [&](void) -> Vec<SI> {
+            ++opi;
+            if (opi == nops) return xout;
+            return (cur.d == lev[l].T0.d) ? lev[l].T1 : lev[l].T0;
+        };
+        for (int q = 0; q < nu1; ++q) {
+            Vec<SI> d = dest();
+            launch(k_smooth<SI>, nb, kBlock, 0, st(), op, B, act, cur, b, d, om);
+            cur = d;
+        }
+        // residual and restriction
+        Vec<SI> zero{};
+        if (cur.d == nullptr) {
+            // no pre-smoothing from a zero guess: residual = b
+            const Geo& gc = lev[l + 1].g;
+            launch(k_restrict<SI>, blocks_for_rows((long long)B * gc.R), kBlock, 0, st(), g, gc, B, act, b,
+                                                                                    lev[l + 1].Bb);
+        } else {
+            launch(k_residual<SI>, nb, kBlock, 0, st(), op, B, act, cur, b, lev[l].Rr);
+            const Geo& gc = lev[l + 1].g;
+            launch(k_restrict<SI>, blocks_for_rows((long long)B * gc.R), kBlock, 0, st(), g, gc, B, act, lev[l].Rr,
+                                                                                    lev[l + 1].Bb);
+        }
+        AAO_LAUNCH_CHECK();
+        AAO_TRY(vcycle(l + 1, stage, B, act, zero, lev[l + 1].Bb, lev[l + 1].X));
+        {
+            Vec<SI> d = dest();
+            launch(k_prolong_add<SI>, nb, kBlock, 0, st(), g, lev[l + 1].g, B, act, lev[l + 1].X, cur, d);
+            cur = d;
+        }
+        for (int q = 0; q < nu2; ++q) {
+            Vec<SI> d = dest();
+            launch(k_smooth<SI>, nb, kBlock, 0, st(), op, B, act, cur, b, d, om);
+            cur = d;
+        }
+        AAO_LAUNCH_CHECK();
+        return AAO_OK;
+    }
+
+    aao_status mg_solve(int stage, int B, const int* act, Vec<SI> b, Vec<SI> out) {
+        Vec<SI> zero{};
+        for (int cyc = 0; cyc < h->opt.mg_cycles; ++cyc) AAO_TRY(vcycle(0, stage, B, act, cyc == 0 ? zero : out, b, out));
+        return AAO_OK;
+    }
+
+    // Z = P_int^{-1} V (items of s*nx), forward or backward stage sweep.
+    aao_status rana(int B, const int* act, Vec<SP> V, Vec<SI> Z, int transpose) {
+        const Geo& g = h->g;
+        const int s = h->s;
+        unsigned nb = blocks_for_rows((long long)B * g.R);
+        for (int t = 0; t < s; ++t) {
+            int i = transpose ? s - 1 - t : t;
+            const double* coef = (transpose ? h->d_LDb : h->d_LDf) + i * s;
+            launch(k_rana_rhs<SP, SI>, nb, kBlock, 0, st(), g, B, act, V, i, Z, s, coef, (A)h->tau, facesA, mgb);
+            AAO_LAUNCH_CHECK();
+            Vec<SI> Zi = shift_vec(Z, (long long)i * g.nx, g.n0);
+            AAO_TRY(mg_solve(i, B, act, mgb, Zi));
+        }
+        return AAO_OK;
+    }
+
+    // ------------------------------------------------------- inner GMRES
+    // Batched GMRES(kin) on Theta_hat (or Theta_hat^T) for B items of s*nx;
+    // rhs item b at src + b*sbs (type SR, unscaled).  On exit Z0/yh/itsh hold the
+    // Krylov solution of every item; out (if given) receives sum_k y_k Z_k.
+    template <class SR>
+    aao_status inner(int B, const SR* src, long long sbs, double* out, long long obs, int transpose) {
+        const Geo& g = h->g;
+        const int s = h->s;
+        const long long item = (long long)s * g.nx;
+        const long long rows = (long long)s * g.R;
+        const unsigned nb = blocks_for_rows((long long)B * rows);
+        const unsigned nbs = blocks_for_rows((long long)B * g.R);
+        Red red = h->red;
+        red.nchunk = h->nchunk_for(B, rows);
+        dim3 rgrid(red.nchunk, B);
+        launch(k_norm<SR>, rgrid, kBlock, 0, st(), g.n0, rows, B, nullptr, src, sbs, red, betah, 1);
+        launch(k_inner_init, (B + 127) / 128, 128, 0, st(), B, kin, betah, activeh, itsh, gh, nonfin);
+        launch(k_scale_store<SP, SR>, nb, kBlock, 0, st(), g.n0, rows, B, activeh, src, sbs, betah, 1, V0);
+        AAO_LAUNCH_CHECK();
+        const long long HS = (long long)(kin + 1) * kin;
+        for (int k = 0; k < kin; ++k) {
+            Vec<SP> Vk = shift_vec(V0, k * vstride, g.n0);
+            Vec<SI> Zk = shift_vec(Z0, k * zstride, g.n0);
+            AAO_TRY(rana(B, activeh, Vk, Zk, transpose));
+            launch(k_theta<SI, A>, nbs, kBlock, 0, st(), g, B, activeh, Zk, wv, item, s, transpose ? h->d_AT : h->d_A,
+                                                     (A)h->tau, facesA);
+            AAO_LAUNCH_CHECK();
+            // modified Gram--Schmidt: h_{0,k} = V_0.w; then w -= h_{i-1,k} V_{i-1}, h_{i,k} = V_i.w
+            Vec<SP> none{};
+            launch(k_mgs<SP, A>, rgrid, kBlock, 0, st(), g.n0, rows, B, activeh, wv, item, none, nullptr, V0, HS,
+                                                     red, Hh + k);
+            for (int i = 1; i <= k + 1; ++i) {
+                Vec<SP> Vp = shift_vec(V0, (i - 1) * vstride, g.n0);
+                Vec<SP> Vn = i <= k ? shift_vec(V0, i * vstride, g.n0) : none;
+                launch(k_mgs<SP, A>, rgrid, kBlock, 0, st(), g.n0, rows, B, activeh, wv, item, Vp,
+                                                         Hh + (i - 1) * kin + k, Vn, HS, red, Hh + i * kin + k);
+            }
+            launch(k_givens, (B + 127) / 128, 128, 0, st(), B, k, kin, Hh, HS, csh, snh, gh, betah, itol, activeh, itsh,
+                                                        nonfin, nullptr);
+            AAO_LAUNCH_CHECK();
+            if (k + 1 < kin) {
+                Vec<SP> Vn = shift_vec(V0, (k + 1) * vstride, g.n0);
+                launch(k_scale_store<SP, A>, nb, kBlock, 0, st(), g.n0, rows, B, activeh, wv, item,
+                                                              Hh + (k + 1) * kin + k, HS, Vn);
+                AAO_LAUNCH_CHECK();
+            }
+        }
+        launch(k_hess_solve, (B + 127) / 128, 128, 0, st(), B, kin, Hh, HS, gh, itsh, yh, brk);
+        launch(k_count_its, 1, 128, 0, st(), B, itsh, itcount);
+        if (out) {
+            Vec<SI> Zc = Z0;
+            launch(k_combine<SI, double>, nb, kBlock, 0, st(), g.n0, rows, B, Zc, zstride, yh, kin, itsh, out, obs, 0);
+        }
+        AAO_LAUNCH_CHECK();
+        return AAO_OK;
+    }
+
+    // ------------------------------------------------------------- P_tilde
+    aao_status apply(const double* r, double* z, int transpose) override {
+        const Geo& g = h->g;
+        const int s = h->s, nt = h->nt;
+        const long long nx = g.nx, nv = h->nv, item = (long long)s * nx;
+        const unsigned nbr = blocks_for_rows(g.R);
+        cudaEventRecord(e0, st());
+        if (!transpose) {
+            AAO_TRY(inner<double>(nt, r + nv, item, z + nv, item, 0));
+            cudaEventRecord(e1, st());
+            long long tot = (nt + 1) * nx;
+            launch(k_schur_g<A>, (unsigned)((tot + 255) / 256), 256, 0, st(), nx, nt, s, r, z + nv, h->d_b, h->tau, wbuf,
+                                                                          z);
+            AAO_LAUNCH_CHECK();
+            for (int n = 0; n < nt; ++n) {
+                launch(k_schur_rhs<A>, nbr, kBlock, 0, st(), g, s, z + n * nx, tbuf, facesA);
+                AAO_TRY(inner<A>(1, tbuf, item, nullptr, 0, 0));
+                launch(k_schur_update<SI, A>, nbr, kBlock, 0, st(), g, s, wbuf + (n + 1) * nx, z + n * nx, Z0, zstride,
+                                                                yh, kin, itsh, h->d_b, h->tau, z + (n + 1) * nx);
+                AAO_LAUNCH_CHECK();
+            }
+            cudaEventRecord(e2, st());
+        } else {
+            // S_tilde^T: backward substitution, u stored in z's v-part (M = I: z_v = u)
+            AAO_CUDA_TRY(cudaMemcpyAsync(z + nt * nx, r + nt * nx, sizeof(double) * nx, cudaMemcpyDeviceToDevice,
+                                         st()));
+            const unsigned nbt = (unsigned)((item + 255) / 256);
+            for (int n = nt - 1; n >= 0; --n) {
+                launch(k_schurT_rhs<A>, nbt, 256, 0, st(), nx, s, z + (n + 1) * nx, h->d_b, tbuf);
+                AAO_TRY(inner<A>(1, tbuf, item, nullptr, 0, 1));
+                Vec<SI> Zc = Z0;
+                launch(k_combine<SI, A>, blocks_for_rows((long long)s * g.R), kBlock, 0, st(), 
+                    g.n0, (long long)s * g.R, 1, Zc, zstride, yh, kin, itsh, qbuf, item, 0);
+                launch(k_schurT_update<A>, nbr, kBlock, 0, st(), g, s, r + n * nx, z + (n + 1) * nx, qbuf, h->tau, facesA,
+                                                             z + n * nx);
+                AAO_LAUNCH_CHECK();
+            }
+            cudaEventRecord(e1, st());
+            long long tot = (long long)nt * item;
+            launch(k_schurT_vrhs<A>, (unsigned)((tot + 255) / 256), 256, 0, st(), nx, nt, s, r + nv, z, h->d_b, h->tau, tV);
+            AAO_LAUNCH_CHECK();
+            AAO_TRY(inner<A>(nt, tV, item, z + nv, item, 1));
+            cudaEventRecord(e2, st());
+        }
+        return AAO_OK;
+    }
+
+    void accumulate_times() override {
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, e0, e1) == cudaSuccess && cudaEventElapsedTime(&b, e1, e2) == cudaSuccess) {
+            t_theta_ms += a;
+            t_schur_ms += b;
+        }
+        cudaGetLastError();
+    }
+
+    // ------------------------------------------------- component entry points
+    aao_status shifted_solve(int stage, const double* b, double* x) override {
+        const Geo& g = h->g;
+        launch(k_scale_store<SI, double>, blocks_for_rows(g.R), kBlock, 0, st(), g.n0, g.R, 1, nullptr, b, g.nx,
+                                                                             nullptr, 0, mgb);
+        AAO_LAUNCH_CHECK();
+        Vec<SI> out = Z0;   // item 0, stage 0 of the first Z basis
+        AAO_TRY(mg_solve(stage, 1, nullptr, mgb, out));
+        launch(k_load<SI, double>, blocks_for_rows(g.R), kBlock, 0, st(), g.n0, g.R, 1, out, x, g.nx);
+        AAO_LAUNCH_CHECK();
+        return AAO_OK;
+    }
+
+    aao_status pint_apply(const double* r, double* y, int transpose) override {
+        const Geo& g = h->g;
+        const long long rows = (long long)h->s * g.R;
+        launch(k_scale_store<SP, double>, blocks_for_rows(rows), kBlock, 0, st(), g.n0, rows, 1, nullptr, r,
+                                                                              (long long)h->s * g.nx, nullptr, 0, V0);
+        AAO_LAUNCH_CHECK();
+        AAO_TRY(rana(1, nullptr, V0, Z0, transpose));
+        launch(k_load<SI, double>, blocks_for_rows(rows), kBlock, 0, st(), g.n0, rows, 1, Z0, y, (long long)h->s * g.nx);
+        AAO_LAUNCH_CHECK();
+        return AAO_OK;
+    }
+
+    aao_status inner_solve(int nblocks, const double* r, double* z, int* its_host) override {
+        if (nblocks < 1 || nblocks > Bmax) {
+            set_error("inner_solve: nblocks must be in 1..nt");
+            return AAO_ERR_ARG;
+        }
+        const long long item = (long long)h->s * h->g.nx;
+        AAO_TRY(inner<double>(nblocks, r, item, z, item, 0));
+        if (its_host) {
+            AAO_CUDA_TRY(cudaMemcpyAsync(its_host, itsh, sizeof(int) * nblocks, cudaMemcpyDeviceToHost, st()));
+            AAO_CUDA_TRY(cudaStreamSynchronize(st()));
+        }
+        return AAO_OK;
+    }
+
+    long long inner_its() override {
+        long long v = 0;
+        cudaMemcpyAsync(&v, itcount, sizeof(long long), cudaMemcpyDeviceToHost, st());
+        cudaStreamSynchronize(st());
+        return v;
+    }
+    void reset_inner_its() override { cudaMemsetAsync(itcount, 0, sizeof(long long), st()); }
+
+    int nonfinite_flag() override {
+        int v[2] = {0, 0};
+        cudaMemcpyAsync(v, nonfin, 2 * sizeof(int), cudaMemcpyDeviceToHost, st());
+        cudaStreamSynchronize(st());
+        return v[0] | v[1];
+    }
+};
+
+}  // namespace aao

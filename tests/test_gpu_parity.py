@@ -1,0 +1,165 @@
+"""GPU (C ABI) vs FP64 oracle, element by element, on seeded inputs.
+
+Tolerances (FP64 path, relative to the reference's max norm):
+  matvec / transpose / rhs       1e-13  (a handful of rounded FP64 ops per entry)
+  V-cycles, Rana sweep           1e-12  (contracting linear maps; reordered sums)
+  inner GMRES, P_tilde apply     1e-11  (nt sequential inner solves in S_tilde)
+  full FGMRES solve              1e-10  (same iteration count as the oracle)
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle.multigrid import Hierarchy
+from oracle.precond import Preconditioner, gmres_fixed
+from oracle.solve import OracleOptions, build, solve as oracle_solve
+
+from gpu_util import host, rel_max, to_dev, torch, zeros
+
+pytestmark = pytest.mark.gpu
+
+OPTS = dict(inner_maxit=3, inner_tol=1e-6, mg_cycles=3, nu1=2, nu2=2, omega=0.8)
+
+
+def make(ns, nt, method="radau", s=2, T=1.0, kappa=None, prec="fp64", **kw):
+    from paper_2609_16863_gb300 import Solver
+    from paper_2609_16863_gb300.tableau import make as tab
+    from gpu_util import dev
+    dev()
+    opts = dict(OPTS)
+    opts.update(kw)
+    S = Solver(ns, T, nt, tableau=tab(method, s), kappa=None if kappa is None else to_dev(kappa),
+               prec_P=prec, inner_maxit=opts["inner_maxit"], inner_tol=opts["inner_tol"],
+               mg_cycles=opts["mg_cycles"], mg_pre=opts["nu1"], mg_post=opts["nu2"], mg_omega=opts["omega"],
+               tol=kw.get("tol", 1e-10), restart=kw.get("restart", 20), maxit=kw.get("maxit", 100))
+    op = build(ns, T, nt, method, s, kappa=kappa)
+    P = Preconditioner(op, ns, opts["inner_maxit"], opts["inner_tol"], opts["mg_cycles"], opts["nu1"],
+                       opts["nu2"], opts["omega"])
+    return S, op, P
+
+
+def kappa_field(ns, seed=3):
+    return np.exp(synth.gaussian_random_field(ns, 0.15, 0.5, synth.rng_for(seed, "kappa"), with_boundary=True))
+
+
+SHAPES = [((12, 10), 3, "radau", 2, False), ((9, 9), 4, "radau", 3, False), ((16, 16), 2, "gauss", 2, False),
+          ((6, 5, 7), 3, "radau", 3, False), ((11, 13), 3, "radau", 3, True), ((7, 6, 5), 2, "radau", 2, True),
+          ((5, 5), 1, "radau", 1, False), ((1, 1), 2, "radau", 2, False), ((33, 17), 5, "radau", 2, False)]
+
+
+@pytest.mark.parametrize("ns,nt,method,s,var", SHAPES)
+def test_matvec_and_transpose(ns, nt, method, s, var):
+    kap = kappa_field(ns) if var else None
+    S, op, _ = make(ns, nt, method, s, kappa=kap)
+    x = synth.random_vector(op.n_st, 21)
+    y = host(S.matvec(to_dev(x), zeros(op.n_st)))
+    assert rel_max(y, op.matvec(x)) <= 1e-13
+    yt = host(S.matvec(to_dev(x), zeros(op.n_st), transpose=True))
+    assert rel_max(yt, op.rmatvec(x)) <= 1e-13
+    # host buffers go through the same entry point
+    yh = np.zeros(op.n_st)
+    S.matvec(x, yh)
+    assert rel_max(yh, op.matvec(x)) <= 1e-13
+
+
+@pytest.mark.parametrize("ns,nt,method,s,var", SHAPES[:4])
+def test_rhs(ns, nt, method, s, var):
+    S, op, _ = make(ns, nt, method, s)
+    u0 = synth.random_vector(op.nx, 1)
+    f = synth.random_vector(op.nx, 2)
+    r = host(S.rhs(to_dev(f), to_dev(u0), zeros(op.n_st)))
+    assert np.array_equal(r, op.rhs(u0, f))
+    ft = synth.random_vector(nt * s * op.nx, 3)
+    r = host(S.rhs(to_dev(ft), to_dev(u0), zeros(op.n_st), f_time_dep=True))
+    assert np.array_equal(r, op.rhs(u0, ft, f_time_dep=True))
+
+
+@pytest.mark.parametrize("ns,nt,method,s,var", SHAPES)
+def test_shifted_solve_vcycles(ns, nt, method, s, var):
+    kap = kappa_field(ns) if var else None
+    S, op, P = make(ns, nt, method, s, kappa=kap)
+    for i in range(s):
+        b = synth.random_vector(op.nx, 30 + i)
+        x = host(S.shifted_solve(i, to_dev(b), zeros(op.nx)))
+        ref = P.mg[i].solve(b, 3)
+        assert rel_max(x, ref) <= 1e-12, (i, rel_max(x, ref))
+
+
+@pytest.mark.parametrize("ns,nt,method,s,var", SHAPES)
+def test_pint_apply(ns, nt, method, s, var):
+    kap = kappa_field(ns) if var else None
+    S, op, P = make(ns, nt, method, s, kappa=kap)
+    r = synth.random_vector(s * op.nx, 40)
+    y = host(S.pint_apply(to_dev(r), zeros(s * op.nx)))
+    assert rel_max(y, P.pint_apply(r)) <= 1e-12
+    yt = host(S.pint_apply(to_dev(r), zeros(s * op.nx), transpose=True))
+    assert rel_max(yt, P.pint_apply_T(r)) <= 1e-12
+
+
+@pytest.mark.parametrize("ns,nt,method,s,var", SHAPES)
+@pytest.mark.parametrize("itol", [0.0, 1e-2])
+def test_inner_solve(ns, nt, method, s, var, itol):
+    kap = kappa_field(ns) if var else None
+    S, op, P = make(ns, nt, method, s, kappa=kap, inner_tol=itol)
+    R = synth.random_vector(nt * s * op.nx, 50).reshape(nt, s * op.nx)
+    R[0] = 0.0                                   # a zero block returns zero
+    z, its = S.inner_solve(nt, to_dev(R.ravel()), zeros(nt * s * op.nx))
+    z = host(z).reshape(nt, -1)
+    for n in range(nt):
+        ref, k = gmres_fixed(P.theta_apply, P.pint_apply, R[n], 3, itol)
+        assert its[n] == k
+        if n == 0:
+            assert not z[0].any()
+        else:
+            assert rel_max(z[n], ref) <= 1e-11, (n, rel_max(z[n], ref))
+
+
+@pytest.mark.parametrize("ns,nt,method,s,var", SHAPES)
+def test_precond_apply(ns, nt, method, s, var):
+    kap = kappa_field(ns) if var else None
+    S, op, P = make(ns, nt, method, s, kappa=kap)
+    r = synth.random_vector(op.n_st, 60)
+    z = host(S.precond_apply(to_dev(r), zeros(op.n_st)))
+    assert rel_max(z, P.apply(r)) <= 1e-11
+    zt = host(S.precond_apply(to_dev(r), zeros(op.n_st), transpose=True))
+    assert rel_max(zt, P.apply_T(r)) <= 1e-11
+
+
+@pytest.mark.parametrize("ns,nt,method,s,var", SHAPES)
+def test_solve_fp64_matches_oracle(ns, nt, method, s, var):
+    kap = kappa_field(ns) if var else None
+    S, op, _ = make(ns, nt, method, s, kappa=kap, tol=1e-10)
+    u0 = synth.gaussian_random_field(ns, 0.2, 1.0, synth.rng_for(5, "u0"))
+    f = synth.gaussian_random_field(ns, 0.2, 1.0, synth.rng_for(5, "f"))
+    x, info = S.solve(to_dev(f), to_dev(u0), zeros(op.n_st))
+    x = host(x)
+    o = OracleOptions(tol=1e-10, **OPTS)
+    ref = oracle_solve(op, ns, op.rhs(u0, f), o)
+    assert info.converged and ref.converged
+    assert info.outer_its == ref.outer_its
+    assert np.linalg.norm(x - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+    # final true residuals agree unless both sit at the FP64 rounding floor (~1e-14)
+    assert abs(info.rel_res - ref.rel_res) <= 1e-3 * ref.rel_res + 1e-13
+
+
+def test_solve_small_2d_closed_form_workload():
+    w = synth.workload_small_2d()
+    S, op, _ = make(w.n, w.nt, "radau", w.s, tol=1e-10, inner_maxit=5, inner_tol=1e-6)
+    x, info = S.solve(to_dev(w.f), to_dev(w.u0), zeros(op.n_st))
+    ref = oracle_solve(op, w.n, op.rhs(w.u0, w.f), OracleOptions(tol=1e-10, inner_maxit=5, inner_tol=1e-6))
+    assert info.outer_its == ref.outer_its
+    assert np.linalg.norm(host(x) - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_mixed_precision_solve_error(prec):
+    ns, nt, s = (32, 32), 8, 3
+    S, op, _ = make(ns, nt, "radau", s, prec=prec, tol=1e-8, inner_maxit=3, inner_tol=1e-3)
+    u0 = synth.gaussian_random_field(ns, 0.1, 1.0, synth.rng_for(7, "u0"))
+    f = synth.gaussian_random_field(ns, 0.1, 1.0, synth.rng_for(7, "f"))
+    x, info = S.solve(to_dev(f), to_dev(u0), zeros(op.n_st))
+    ref = oracle_solve(op, ns, op.rhs(u0, f), OracleOptions(tol=1e-13, inner_maxit=5, inner_tol=1e-6))
+    err = np.linalg.norm(host(x) - ref.x) / np.linalg.norm(ref.x)
+    print(f"{prec}: outer {info.outer_its} rel_res {info.rel_res:.2e} err vs FP64 oracle {err:.2e}")
+    assert info.converged and info.rel_res <= 1e-8
+    assert err <= 1e-7
