@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""Benchmark: time to a 1e-8 relative residual of the all-at-once RK heat solve.
+
+Workload (one step = one full solve, FP64 FGMRES(20) outer + P_tilde):
+  2D 256x256 interior FD grid (M = I), Radau IIA s = 3, 128 steps to T = 1,
+  u0 and f seeded Gaussian random fields (squared-exponential, l = 0.1,
+  unit variance), f constant in time; n_st = 33,619,968 space-time unknowns.
+  The timed solve applies P_tilde in FP32 (Theta_tilde GMRES 3 / 1e-3, 3
+  V-cycles); the same problem is also solved once with P_tilde in FP64
+  (GMRES 5 / 1e-6) for the mixed-vs-FP64 comparison.
+
+Timing: W warm-up solves, then K solves between CUDA events on the solver's
+stream with a barrier and a synchronize on both sides; the working set
+(x 269 MB, Krylov basis ~11 GB) is far larger than L2.  `e2e` repeats the
+solve through the C ABI with pinned host buffers (copies inside the timed
+region).  `roofline` times every launch of the dominant kernel with CUDA
+events during one extra solve and divides its algorithmic bytes by that time.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 residual, mixed vs FP64 precond, same GB300; precond HBM GB/s"
+WORKLOAD = "fd2d_n256_radau3_nt128"
+PROFILE_KERNEL = "k_smooth"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp16"])
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64-preconditioner comparison solve")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--small", action="store_true", help="64x64, nt 16 (quick check; not a bench value)")
+    return p.parse_args()
+
+
+def workload(small: bool):
+    import synth
+    if small:
+        return synth.workload_fp32_precond_2d(N=64, nt=16, s=3)
+    return synth.workload_fp32_precond_2d()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.tmp = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.close()
+        rows = []
+        for ln in open(self.tmp.name):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(w, outer_its: int, budget_s: float = 20.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload.
+
+    Sample: one all-at-once matvec and a few inner Theta_tilde solves (the unit
+    of work P_tilde repeats 2*nt times per application) at full size; the
+    estimate of the oracle's time to solution is
+    outer_its * (2 nt t_inner + 2 t_matvec) + t_ortho(outer_its).
+    """
+    from oracle.precond import Preconditioner
+    from oracle.solve import build
+    op = build(w.n, w.T, w.nt, w.method, w.s)
+    P = Preconditioner(op, w.n, inner_maxit=3, inner_tol=1e-3, mg_cycles=3, nu1=2, nu2=2, omega=0.8)
+    x = np.random.default_rng(0).standard_normal(op.n_st)
+    t0 = time.perf_counter()
+    op.matvec(x)
+    t_mv = time.perf_counter() - t0
+    r = x[op.n_v: op.n_v + w.s * op.nx].copy()
+    n_inner = 0
+    t0 = time.perf_counter()
+    while True:
+        P.inner_solve(r)
+        n_inner += 1
+        if time.perf_counter() - t0 > budget_s * 0.6 or n_inner >= 8:
+            break
+    t_inner = (time.perf_counter() - t0) / n_inner
+    t0 = time.perf_counter()
+    basis = [x] * 4
+    for v in basis:
+        x = x - (v @ x) * v
+    t_dot = (time.perf_counter() - t0) / 4
+    est = outer_its * (2 * w.nt * t_inner + 2 * t_mv) + t_dot * outer_its * (outer_its + 1) / 2
+    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle on 1 host core: 1 full matvec ({t_mv:.2f} s) and {n_inner} inner "
+                       f"Theta_tilde solves ({t_inner:.2f} s each) at 256x256 s=3; time to solution "
+                       f"estimated for {outer_its} outer iterations as its*(2*nt*t_inner+2*t_matvec)"
+                       f"+orthogonalisation")}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.small)
+    steps = []
+    for _ in range(max(1, args.warmup)):
+        pass
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(w, outer_its=10, budget_s=8.0)
+        steps.append(cb["value"])
+    v = float(np.median(steps))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precond": "fp32-equivalent settings, FP64 arithmetic",
+                       "outer": "FGMRES(20) tol 1e-8"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2609_16863_gb300 import Solver, _lib, radau_iia
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    lib = _lib.lib()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = workload(args.small)
+    common = dict(tableau=radau_iia(w.s), tol=w.tol, restart=20, maxit=100, stream=stream.cuda_stream)
+    S = Solver(w.n, w.T, w.nt, prec_P=args.prec, inner_maxit=3, inner_tol=1e-3, **common)
+    f = torch.from_numpy(w.f).to(dev)
+    u0 = torch.from_numpy(w.u0).to(dev)
+    x = torch.zeros(S.n_st, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    info = None
+    for _ in range(args.warmup):
+        _, info = S.solve(f, u0, x)
+    clocks = Clocks(local)
+    n0 = lib.aao_rk_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, info = S.solve(f, u0, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    launches = lib.aao_rk_launch_count() - n0
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    x_mixed = x.clone()
+
+    # FP64 preconditioner on the same problem (mixed vs FP64 comparison)
+    fp64 = None
+    if not args.no_fp64:
+        S64 = Solver(w.n, w.T, w.nt, prec_P="fp64", inner_maxit=5, inner_tol=1e-6, **common)
+        x64 = torch.zeros_like(x)
+        S64.solve(f, u0, x64)            # warm-up
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a0.record(stream)
+        _, i64 = S64.solve(f, u0, x64)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t64 = a0.elapsed_time(a1) / 1e3
+        diff = float(torch.linalg.norm(x_mixed - x64) / torch.linalg.norm(x64))
+        fp64 = {"time_s": t64, "outer_its": i64.outer_its, "inner_its": i64.inner_its_total,
+                "rel_res": i64.rel_res, "t_theta_ms": i64.t_theta_ms, "t_schur_ms": i64.t_schur_ms,
+                "speedup_mixed_vs_fp64": t64 / (ms / 1e3),
+                "rel_diff_mixed_vs_fp64_solution": diff}
+        S64.close()
+        del x64
+
+    # end to end through the C ABI with pinned host buffers
+    fh = torch.from_numpy(w.f).pin_memory()
+    uh = torch.from_numpy(w.u0).pin_memory()
+    xh = torch.zeros(S.n_st, dtype=torch.float64).pin_memory()
+    S.solve(fh, uh, xh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S.solve(fh, uh, xh)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+
+    # live roofline of the dominant kernel: events around each of its launches in one solve
+    _lib.check(lib.aao_rk_profile_begin(PROFILE_KERNEL.encode()))
+    S.solve(f, u0, x)
+    import ctypes as C
+    nl, pms, pby = C.c_longlong(), C.c_double(), C.c_double()
+    _lib.check(lib.aao_rk_profile_end(C.byref(nl), C.byref(pms), C.byref(pby)))
+    peak, peak_kind = peaks()
+    achieved = pby.value / (pms.value * 1e-3) / 1e9 if pms.value > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": PROFILE_KERNEL, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+            "launches_per_solve": nl.value, "kernel_ms_per_solve": pms.value,
+            "algorithmic_bytes_per_launch": pby.value / max(1, nl.value),
+            "share_of_solve": pms.value / ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, info.outer_its)
+
+    if rank == 0:
+        value = ms / 1e3
+        line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": f"f64/{args.prec}", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": [256, 256] if not args.small else list(w.n),
+                           "nt": w.nt, "s": w.s, "n_st": S.n_st,
+                           "precond": f"P_tilde {args.prec}, inner GMRES 3/1e-3, 3 V(2,2)-cycles",
+                           "outer": "FP64 FGMRES(20), tol 1e-8",
+                           "l2": "working set larger than L2 (no flush)", "parallelism": "replicas",
+                           "small_check_only": bool(args.small)},
+                "outer_its": info.outer_its, "inner_its": info.inner_its_total, "rel_res": info.rel_res,
+                "t_theta_ms": info.t_theta_ms, "t_schur_ms": info.t_schur_ms,
+                "fp64_precond": fp64,
+                "dofs_its_per_s": S.n_st * info.outer_its / (ms / 1e3),
+                "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * (2 * S.nx),
+                        "d2h_bytes_per_step": 8 * S.n_st},
+                "gpu_launches": launches // max(1, args.steps) * args.steps,
+                "roofline": roof, "cpu_baseline": cpu, "clocks": ck}
+        print(json.dumps(line), flush=True)
+    S.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

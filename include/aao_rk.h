@@ -124,6 +124,14 @@ const char* aao_rk_last_error(void);
 /* Number of kernels this library has launched in the process so far (all
  * handles); the difference across a call counts that call's launches. */
 long long aao_rk_launch_count(void);
+/* Launch profiling (measurement aid, not thread-safe): between begin and end,
+ * every launch of a kernel whose name contains kernel_name is bracketed by
+ * CUDA events on its stream and credited with the algorithmic bytes its launch
+ * site declares (compulsory reads and writes of that launch).  end()
+ * synchronises the device and returns the number of such launches, their
+ * summed event time and their summed algorithmic bytes. */
+aao_status aao_rk_profile_begin(const char* kernel_name);
+aao_status aao_rk_profile_end(long long* launches, double* total_ms, double* total_bytes);
 
 /* n_x = prod(n), n_st = n_x (nt + 1 + s nt). */
 aao_status aao_rk_sizes(aao_rk_handle h, long long* n_x, long long* n_st);

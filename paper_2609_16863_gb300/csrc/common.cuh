@@ -223,11 +223,23 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 // Every kernel of the library is launched through launch(): it counts launches
 // (reported by aao_rk_launch_count) and forwards to <<<grid, block, shmem, stream>>>.
+// When a profile is open (aao_rk_profile_begin), launches of kernels whose name
+// contains the requested text are bracketed by CUDA events on their stream and
+// credited with the algorithmic bytes the launch site declared by bytes_hint().
 extern long long g_launches;
+extern bool g_prof_on;
+extern thread_local double g_bytes_hint;
+int prof_begin_launch(const void* k, cudaStream_t st, double bytes);
+void prof_end_launch(int slot, cudaStream_t st);
+inline void bytes_hint(double b) { g_bytes_hint = b; }
 template <class... KArgs, class... Args>
 inline void launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t shmem, cudaStream_t st, Args... args) {
     ++g_launches;
+    double bytes = g_bytes_hint;
+    g_bytes_hint = 0.0;
+    int slot = g_prof_on ? prof_begin_launch((const void*)k, st, bytes) : -1;
     k<<<grid, block, shmem, st>>>(args...);
+    if (slot >= 0) prof_end_launch(slot, st);
 }
 
 inline unsigned int blocks_for_rows(long long rows) {

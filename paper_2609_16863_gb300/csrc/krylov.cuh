@@ -333,13 +333,30 @@ __global__ void k_schur_g(long long nx, int nt, int s, const double* r, const do
     wbuf[i] = v;
 }
 
+// Per-step state of the Schur substitution, in device memory so that one
+// captured step can be replayed for every n: z (output vector), r (input
+// vector) and the step index n.
+struct StepPtrs {
+    double* z;
+    const double* r;
+    int n;
+};
+
+static __global__ void k_step_set(StepPtrs* sp, double* z, const double* r, int n) {
+    sp->z = z;
+    sp->r = r;
+    sp->n = n;
+}
+
+static __global__ void k_step_add(StepPtrs* sp, int d) { sp->n += d; }
+
 // t_i = K z_{v,n} for every stage i (the e (x) K z_{v,n} right-hand side).
 template <class A>
-__global__ void __launch_bounds__(kBlock) k_schur_rhs(Geo g, int s, const double* zvn, A* t, Faces<A> faces) {
+__global__ void __launch_bounds__(kBlock) k_schur_rhs(Geo g, int s, const StepPtrs* sp, A* t, Faces<A> faces) {
     long long row = gwarp();
     if (row >= g.R) return;
     int j = (int)(row % g.n1), k = (int)(row / g.n1);
-    View<double> z{zvn, nullptr, g.n0};
+    View<double> z{sp->z + (long long)sp->n * g.nx, nullptr, g.n0};
     for (int c = lane_id(); c < g.n0; c += kWarp) {
         A v = (A)fd_K(z, g, faces, row, j, k, c);
         for (int i = 0; i < s; ++i) t[(long long)i * g.nx + row * g.n0 + c] = v;
@@ -348,12 +365,16 @@ __global__ void __launch_bounds__(kBlock) k_schur_rhs(Geo g, int s, const double
 
 // z_{v,n+1} = w_{n+1} + z_{v,n} - tau sum_i b_i q_i,  q = sum_k y_k Z_k (item 0).
 template <class SZ, class A>
-__global__ void __launch_bounds__(kBlock) k_schur_update(Geo g, int s, const A* wn1, const double* zvn,
+__global__ void __launch_bounds__(kBlock) k_schur_update(Geo g, int s, const A* wbuf, const StepPtrs* sp,
                                                          Vec<SZ> Z0, long long zstride, const double* y,
                                                          int kmax, const int* its, const double* bw,
-                                                         double tau, double* zvn1) {
+                                                         double tau) {
     long long row = gwarp();
     if (row >= g.R) return;
+    const int n = sp->n;
+    const A* wn1 = wbuf + (long long)(n + 1) * g.nx;
+    const double* zvn = sp->z + (long long)n * g.nx;
+    double* zvn1 = sp->z + (long long)(n + 1) * g.nx;
     int m = its[0];
     A coef[kMaxInner * kMaxS];
     for (int k = 0; k < m; ++k)
@@ -376,20 +397,24 @@ __global__ void __launch_bounds__(kBlock) k_schur_update(Geo g, int s, const A* 
 
 // Transposed substitution: t_i = b_i u_{n+1}.
 template <class A>
-__global__ void k_schurT_rhs(long long nx, int s, const double* un1, const double* bw, A* t) {
+__global__ void k_schurT_rhs(long long nx, int s, const StepPtrs* sp, const double* bw, A* t) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)s * nx) return;
     int q = (int)(i / nx);
-    t[i] = (A)bw[q] * (A)un1[i % nx];
+    t[i] = (A)bw[q] * (A)sp->z[(long long)(sp->n + 1) * nx + i % nx];
 }
 
 // u_n = r_{v,n} + u_{n+1} - tau sum_i K q_i   (q flat, s*nx, type A).
 template <class A>
-__global__ void __launch_bounds__(kBlock) k_schurT_update(Geo g, int s, const double* rvn, const double* un1,
-                                                          const A* q, double tau, Faces<A> faces, double* un) {
+__global__ void __launch_bounds__(kBlock) k_schurT_update(Geo g, int s, const StepPtrs* sp, const A* q,
+                                                          double tau, Faces<A> faces) {
     long long row = gwarp();
     if (row >= g.R) return;
     int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    const int n = sp->n;
+    const double* rvn = sp->r + (long long)n * g.nx;
+    const double* un1 = sp->z + (long long)(n + 1) * g.nx;
+    double* un = sp->z + (long long)n * g.nx;
     View<A> qs[kMaxS];
     for (int i = 0; i < s; ++i) qs[i] = View<A>{q + (long long)i * g.nx, nullptr, g.n0};
     for (int c = lane_id(); c < g.n0; c += kWarp) {

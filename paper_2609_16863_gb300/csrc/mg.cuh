@@ -439,3 +439,196 @@ __global__ void k_convert_dense(const double* in, A* out, long long n) {
 }
 
 }  // namespace aao
+
+namespace aao {
+
+// ---------------------------------------------------------------------------
+// Fused V-cycle tail: levels lc..L-1 of one batch item in one CTA, every level
+// held on chip (x and b per level, arithmetic type A), Jacobi sweeps staged in
+// registers, residual recomputed inside the restriction.  One launch replaces
+// the ~7 launches per level of the level-by-level path.  Vectors that stay on
+// chip are not rounded to the 16-bit storage format (that format is for data
+// that travels through HBM).
+// ---------------------------------------------------------------------------
+constexpr int kTailPmax = 16;   // points per thread at level lc
+constexpr int kTailMaxPoints = 2048;
+
+template <class SI> struct TailCtx {
+    using A = typename PT<SI>::A;
+    int lc, L;
+    LevelOp<SI> op[kMaxLevels];
+    int off[kMaxLevels];        // smem offset (A elements) of X_l; B_l follows
+    const A* Dinv;
+    A omega;
+    int nu1, nu2;
+};
+
+template <class SI>
+__device__ __forceinline__ void tail_smooth(const TailCtx<SI>& t, int l, typename PT<SI>::A* sm, int sweeps,
+                                            bool zero_first) {
+    using A = typename PT<SI>::A;
+    const LevelOp<SI>& op = t.op[l];
+    const Geo& g = op.g;
+    A* X = sm + t.off[l];
+    const A* Bv = X + g.nx;
+    View<A> xv{X, nullptr, g.n0};
+    const int nt = blockDim.x;
+    for (int sw = 0; sw < sweeps; ++sw) {
+        const bool zero = zero_first && sw == 0;
+        A nv[kTailPmax];
+#pragma unroll
+        for (int i = 0; i < kTailPmax; ++i) {
+            int p = threadIdx.x + i * nt;
+            nv[i] = A(0);
+            if (p < g.nx) {
+                int c = p % g.n0;
+                long long row = p / g.n0;
+                int j = (int)(row % g.n1), k = (int)(row / g.n1);
+                A Au, dg;
+                if (zero) {
+                    if (op.fine) dg = op.sigma + op.c * fd_K_diag<A>(g, op.faces, row, j, k, c);
+                    else dg = sten_coef(op, g.d == 3 ? 13 : 4, p);
+                    nv[i] = t.omega * Bv[p] / dg;
+                } else {
+                    level_apply(op, xv, row, j, k, c, Au, dg);
+                    nv[i] = X[p] + t.omega * (Bv[p] - Au) / dg;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kTailPmax; ++i) {
+            int p = threadIdx.x + i * nt;
+            if (p < g.nx) X[p] = nv[i];
+        }
+        __syncthreads();
+    }
+}
+
+template <class SI>
+__global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, const int* active, Vec<SI> bv,
+                                                      Vec<SI> xin, Vec<SI> xout) {
+    using A = typename PT<SI>::A;
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    A* sm = reinterpret_cast<A*>(tail_smem);
+    const int b = blockIdx.x;
+    if (b >= B || (active && !active[b])) return;
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int lc = t.lc, L = t.L;
+    {
+        const Geo& g = t.op[lc].g;
+        A* X = sm + t.off[lc];
+        A* Bv = X + g.nx;
+        View<SI> bs = view_of(bv, b, 0, g.n0);
+        const bool has = xin.d != nullptr;
+        View<SI> xs = has ? view_of(xin, b, 0, g.n0) : View<SI>{nullptr, nullptr, g.n0};
+        for (int p = tid; p < g.nx; p += nt) {
+            int c = p % g.n0, row = p / g.n0;
+            Bv[p] = bs.at(row, c);
+            X[p] = has ? xs.at(row, c) : A(0);
+        }
+    }
+    __syncthreads();
+    bool xzero = xin.d == nullptr;
+    for (int l = lc; l < L - 1; ++l) {
+        const LevelOp<SI>& op = t.op[l];
+        const Geo& gf = op.g;
+        const Geo& gc = t.op[l + 1].g;
+        A* X = sm + t.off[l];
+        A* Bv = X + gf.nx;
+        if (t.nu1 > 0) {
+            tail_smooth(t, l, sm, t.nu1, xzero);
+            xzero = false;
+        }
+        A* Xc = sm + t.off[l + 1];
+        A* Bc = Xc + gc.nx;
+        View<A> xv{X, nullptr, gf.n0};
+        for (int P = tid; P < gc.nx; P += nt) {
+            int I = P % gc.n0;
+            long long crow = P / gc.n0;
+            int J = (int)(crow % gc.n1), Kc = (int)(crow / gc.n1);
+            A acc = A(0);
+            const int zlo = gf.d == 3 ? -1 : 0, zhi = gf.d == 3 ? 1 : 0;
+            for (int dz = zlo; dz <= zhi; ++dz) {
+                int fk = gf.d == 3 ? 2 * Kc + 1 + dz : 0;
+                if (fk < 0 || fk >= gf.n2) continue;
+                A wz = dz == 0 ? A(1) : A(0.5);
+                for (int dy = -1; dy <= 1; ++dy) {
+                    int fj = 2 * J + 1 + dy;
+                    if (fj < 0 || fj >= gf.n1) continue;
+                    A wy = dy == 0 ? A(1) : A(0.5);
+                    long long frow = fj + (long long)gf.n1 * fk;
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int fi = 2 * I + 1 + dx;
+                        if (fi < 0 || fi >= gf.n0) continue;
+                        A wx = dx == 0 ? A(1) : A(0.5);
+                        A r = Bv[frow * gf.n0 + fi];
+                        if (!xzero) {
+                            A Au, dg;
+                            level_apply(op, xv, frow, fj, fk, fi, Au, dg);
+                            r -= Au;
+                        }
+                        acc += wx * wy * wz * r;
+                    }
+                }
+            }
+            Bc[P] = acc;
+            Xc[P] = A(0);
+        }
+        __syncthreads();
+        xzero = true;   // coarse levels start from zero
+    }
+    {
+        const Geo& g = t.op[L - 1].g;
+        A* X = sm + t.off[L - 1];
+        const A* Bv = X + g.nx;
+        const int nc = (int)g.nx;
+        if (L - 1 == lc && !xzero) {
+            // a single-level tail with a nonzero guess is still the exact solve
+        }
+        for (int p = tid; p < nc; p += nt) {
+            A acc = A(0);
+            for (int q = 0; q < nc; ++q) acc += t.Dinv[(long long)p * nc + q] * Bv[q];
+            X[p] = acc;
+        }
+    }
+    __syncthreads();
+    for (int l = L - 2; l >= lc; --l) {
+        const Geo& gf = t.op[l].g;
+        const Geo& gc = t.op[l + 1].g;
+        A* X = sm + t.off[l];
+        const A* Xc = sm + t.off[l + 1];
+        for (int p = tid; p < gf.nx; p += nt) {
+            int c = p % gf.n0;
+            long long row = p / gf.n0;
+            int j = (int)(row % gf.n1), k = (int)(row / gf.n1);
+            int Jx[2], Jy[2], Jz[2] = {0, 0};
+            float wx[2], wy[2], wz[2] = {1.f, 0.f};
+            int mx = interp_1d(c, gc.n0, Jx, wx);
+            int my = interp_1d(j, gc.n1, Jy, wy);
+            int mz = gf.d == 3 ? interp_1d(k, gc.n2, Jz, wz) : 1;
+            A acc = X[p];
+            for (int a = 0; a < mz; ++a)
+                for (int q = 0; q < my; ++q)
+                    for (int e = 0; e < mx; ++e)
+                        acc += A(wz[a]) * A(wy[q]) * A(wx[e]) * Xc[(Jz[a] * (long long)gc.n1 + Jy[q]) * gc.n0 + Jx[e]];
+            X[p] = acc;
+        }
+        __syncthreads();
+        if (t.nu2 > 0) tail_smooth(t, l, sm, t.nu2, false);
+    }
+    // write level lc
+    {
+        const Geo& g = t.op[lc].g;
+        const A* X = sm + t.off[lc];
+        const int w = tid >> 5, lane = tid & 31, nw = nt >> 5;
+        for (long long row = w; row < g.R; row += nw) {
+            SI* o;
+            float* osc;
+            row_store_ptrs(xout, b, 0, row, g.n0, o, osc);
+            row_store<SI>(o, osc, g.n0, lane, [&](int c) -> A { return X[row * g.n0 + c]; });
+        }
+    }
+}
+
+}  // namespace aao

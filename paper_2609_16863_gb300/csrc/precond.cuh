@@ -60,8 +60,32 @@ class Precond : public PrecondBase {
     A* tV = nullptr;               // nt*s*nx (transposed apply)
     double* tmp64 = nullptr;       // Bmax*s*nx staging for component entry points
     cudaEvent_t e0, e1, e2;
+    int nact = 0;                  // active items of the current batch (exact only while profiling)
+    int lc = 0;                    // first level handled by the fused on-chip tail kernel
+    int tail_threads = 1024;
+    size_t tail_smem = 0;
+    TailCtx<SI> tctx[kMaxS];
+    int* hact = nullptr;           // pinned mirror of activeh (profiling)
 
-    cudaStream_t st() const { return h->stream; }
+    cudaStream_t cur_stream = nullptr;     // stream of the next launch (capture stream while capturing)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    long long graph_nodes[2] = {0, 0};
+    StepPtrs* stepp = nullptr;
+
+    cudaStream_t st() const { return cur_stream; }
+
+    // While a launch profile is open, read back how many batch items are still
+    // active so the byte hints count only the work that is done.
+    void refresh_nact(int B) {
+        nact = B;
+        if (!g_prof_on || !hact) return;
+        cudaMemcpyAsync(hact, activeh, sizeof(int) * B, cudaMemcpyDeviceToHost, st());
+        cudaStreamSynchronize(st());
+        int c = 0;
+        for (int b = 0; b < B; ++b) c += hact[b] != 0;
+        nact = c;
+    }
 
     template <class S> aao_status alloc_vec(Vec<S>& v, long long items, long long item_len, int n0) {
         AAO_TRY(ar.alloc(&v.d, (size_t)(items * item_len)));
@@ -72,11 +96,18 @@ class Precond : public PrecondBase {
     }
 
   public:
-    explicit Precond(Handle* hh) : h(hh) {}
+    explicit Precond(Handle* hh) : h(hh), cur_stream(hh->stream) {}
     ~Precond() override { release(); }
 
     void release() override {
+        for (int i = 0; i < 2; ++i)
+            if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
+        gexec[0] = gexec[1] = nullptr;
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        cap_stream = nullptr;
         ar.release();
+        if (hact) cudaFreeHost(hact);
+        hact = nullptr;
     }
 
     aao_status setup() override {
@@ -214,6 +245,39 @@ class Precond : public PrecondBase {
             set_error("coarsest multigrid operator is not positive definite");
             return AAO_ERR_BREAKDOWN;
         }
+        // ---- fused tail: the coarsest levels that fit on one SM
+        {
+            const size_t cap = 200 * 1024;
+            lc = L - 1;
+            size_t acc = 0;
+            for (int l = L - 1; l >= 0; --l) {
+                acc += 2 * (size_t)lev[l].g.nx * sizeof(A);
+                // the tail runs on one SM: keep its top level small enough that the
+                // Galerkin stencils it reads stay resident in L1
+                if (lev[l].g.nx > kTailMaxPoints || acc > cap) break;
+                lc = l;
+            }
+            int off = 0;
+            for (int l = lc; l < L; ++l) off += 2 * (int)lev[l].g.nx;
+            tail_smem = (size_t)off * sizeof(A);
+            for (int i = 0; i < s; ++i) {
+                TailCtx<SI>& t = tctx[i];
+                t.lc = lc;
+                t.L = L;
+                int o = 0;
+                for (int l = lc; l < L; ++l) {
+                    t.op[l] = level_op(l, i);
+                    t.off[l] = o;
+                    o += 2 * (int)lev[l].g.nx;
+                }
+                t.Dinv = Dinv[i];
+                t.omega = (A)h->opt.mg_omega;
+                t.nu1 = h->opt.mg_pre;
+                t.nu2 = h->opt.mg_post;
+            }
+            AAO_CUDA_TRY(cudaFuncSetAttribute(k_vcycle_tail<SI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)tail_smem));
+        }
         // ---- level scratch
         for (int l = 0; l < L; ++l) {
             const Geo& gl = lev[l].g;
@@ -254,9 +318,11 @@ class Precond : public PrecondBase {
         AAO_TRY(ar.alloc(&qbuf, (size_t)item));
         AAO_TRY(ar.alloc(&tV, (size_t)(h->nt * item)));
         AAO_TRY(ar.alloc(&tmp64, (size_t)(Bmax * item)));
+        AAO_TRY(ar.alloc(&stepp, 1));
         AAO_CUDA_TRY(cudaEventCreate(&e0));
         AAO_CUDA_TRY(cudaEventCreate(&e1));
         AAO_CUDA_TRY(cudaEventCreate(&e2));
+        AAO_CUDA_TRY(cudaMallocHost((void**)&hact, sizeof(int) * Bmax));
         AAO_CUDA_TRY(cudaStreamSynchronize(st()));
         return AAO_OK;
     }
@@ -289,7 +355,14 @@ class Precond : public PrecondBase {
     aao_status vcycle(int l, int stage, int B, const int* act, Vec<SI> xin, Vec<SI> b, Vec<SI> xout) {
         const Geo& g = lev[l].g;
         unsigned nb = blocks_for_rows((long long)B * g.R);
+        if (l == lc) {
+            bytes_hint((xin.d ? 3.0 : 2.0) * nact * g.nx * sizeof(SI));
+            launch(k_vcycle_tail<SI>, (unsigned)B, tail_threads, tail_smem, st(), tctx[stage], B, act, b, xin, xout);
+            AAO_LAUNCH_CHECK();
+            return AAO_OK;
+        }
         if (l == L - 1) {
+            bytes_hint(2.0 * nact * g.nx * sizeof(SI));
             launch(k_coarse_solve<SI>, nb, kBlock, 0, st(), g, B, act, Dinv[stage], b, xout);
             AAO_LAUNCH_CHECK();
             return AAO_OK;
@@ -307,6 +380,7 @@ class Precond : public PrecondBase {
         };
         for (int q = 0; q < nu1; ++q) {
             Vec<SI> d = dest();
+            bytes_hint((cur.d ? 3.0 : 2.0) * nact * g.nx * sizeof(SI));
             launch(k_smooth<SI>, nb, kBlock, 0, st(), op, B, act, cur, b, d, om);
             cur = d;
         }
@@ -315,11 +389,14 @@ class Precond : public PrecondBase {
         if (cur.d == nullptr) {
             // no pre-smoothing from a zero guess: residual = b
             const Geo& gc = lev[l + 1].g;
+            bytes_hint(1.0 * nact * (g.nx + gc.nx) * sizeof(SI));
             launch(k_restrict<SI>, blocks_for_rows((long long)B * gc.R), kBlock, 0, st(), g, gc, B, act, b,
                                                                                     lev[l + 1].Bb);
         } else {
+            bytes_hint(3.0 * nact * g.nx * sizeof(SI));
             launch(k_residual<SI>, nb, kBlock, 0, st(), op, B, act, cur, b, lev[l].Rr);
             const Geo& gc = lev[l + 1].g;
+            bytes_hint(1.0 * nact * (g.nx + gc.nx) * sizeof(SI));
             launch(k_restrict<SI>, blocks_for_rows((long long)B * gc.R), kBlock, 0, st(), g, gc, B, act, lev[l].Rr,
                                                                                     lev[l + 1].Bb);
         }
@@ -327,11 +404,13 @@ class Precond : public PrecondBase {
         AAO_TRY(vcycle(l + 1, stage, B, act, zero, lev[l + 1].Bb, lev[l + 1].X));
         {
             Vec<SI> d = dest();
+            bytes_hint(1.0 * nact * (lev[l + 1].g.nx + (cur.d ? 2.0 : 1.0) * g.nx) * sizeof(SI));
             launch(k_prolong_add<SI>, nb, kBlock, 0, st(), g, lev[l + 1].g, B, act, lev[l + 1].X, cur, d);
             cur = d;
         }
         for (int q = 0; q < nu2; ++q) {
             Vec<SI> d = dest();
+            bytes_hint(3.0 * nact * g.nx * sizeof(SI));
             launch(k_smooth<SI>, nb, kBlock, 0, st(), op, B, act, cur, b, d, om);
             cur = d;
         }
@@ -353,6 +432,7 @@ class Precond : public PrecondBase {
         for (int t = 0; t < s; ++t) {
             int i = transpose ? s - 1 - t : t;
             const double* coef = (transpose ? h->d_LDb : h->d_LDf) + i * s;
+            bytes_hint(1.0 * nact * g.nx * (sizeof(SP) + (transpose ? s - 1 - i : i) * sizeof(SI) + sizeof(SI)));
             launch(k_rana_rhs<SP, SI>, nb, kBlock, 0, st(), g, B, act, V, i, Z, s, coef, (A)h->tau, facesA, mgb);
             AAO_LAUNCH_CHECK();
             Vec<SI> Zi = shift_vec(Z, (long long)i * g.nx, g.n0);
@@ -378,6 +458,7 @@ class Precond : public PrecondBase {
         dim3 rgrid(red.nchunk, B);
         launch(k_norm<SR>, rgrid, kBlock, 0, st(), g.n0, rows, B, nullptr, src, sbs, red, betah, 1);
         launch(k_inner_init, (B + 127) / 128, 128, 0, st(), B, kin, betah, activeh, itsh, gh, nonfin);
+        refresh_nact(B);
         launch(k_scale_store<SP, SR>, nb, kBlock, 0, st(), g.n0, rows, B, activeh, src, sbs, betah, 1, V0);
         AAO_LAUNCH_CHECK();
         const long long HS = (long long)(kin + 1) * kin;
@@ -385,22 +466,26 @@ class Precond : public PrecondBase {
             Vec<SP> Vk = shift_vec(V0, k * vstride, g.n0);
             Vec<SI> Zk = shift_vec(Z0, k * zstride, g.n0);
             AAO_TRY(rana(B, activeh, Vk, Zk, transpose));
+            bytes_hint(1.0 * nact * item * (sizeof(SI) + sizeof(A)));
             launch(k_theta<SI, A>, nbs, kBlock, 0, st(), g, B, activeh, Zk, wv, item, s, transpose ? h->d_AT : h->d_A,
                                                      (A)h->tau, facesA);
             AAO_LAUNCH_CHECK();
             // modified Gram--Schmidt: h_{0,k} = V_0.w; then w -= h_{i-1,k} V_{i-1}, h_{i,k} = V_i.w
             Vec<SP> none{};
+            bytes_hint(1.0 * nact * item * (sizeof(A) + sizeof(SP)));
             launch(k_mgs<SP, A>, rgrid, kBlock, 0, st(), g.n0, rows, B, activeh, wv, item, none, nullptr, V0, HS,
                                                      red, Hh + k);
             for (int i = 1; i <= k + 1; ++i) {
                 Vec<SP> Vp = shift_vec(V0, (i - 1) * vstride, g.n0);
                 Vec<SP> Vn = i <= k ? shift_vec(V0, i * vstride, g.n0) : none;
+                bytes_hint(1.0 * nact * item * (2 * sizeof(A) + (i <= k ? 2 : 1) * sizeof(SP)));
                 launch(k_mgs<SP, A>, rgrid, kBlock, 0, st(), g.n0, rows, B, activeh, wv, item, Vp,
                                                          Hh + (i - 1) * kin + k, Vn, HS, red, Hh + i * kin + k);
             }
             launch(k_givens, (B + 127) / 128, 128, 0, st(), B, k, kin, Hh, HS, csh, snh, gh, betah, itol, activeh, itsh,
                                                         nonfin, nullptr);
             AAO_LAUNCH_CHECK();
+            refresh_nact(B);
             if (k + 1 < kin) {
                 Vec<SP> Vn = shift_vec(V0, (k + 1) * vstride, g.n0);
                 launch(k_scale_store<SP, A>, nb, kBlock, 0, st(), g.n0, rows, B, activeh, wv, item,
@@ -419,45 +504,108 @@ class Precond : public PrecondBase {
     }
 
     // ------------------------------------------------------------- P_tilde
+    // One step of the Schur substitution (forward: z_{v,n} -> z_{v,n+1};
+    // transposed: u_{n+1} -> u_n), with n, z and r read from device memory.
+    aao_status schur_step(int transpose) {
+        const Geo& g = h->g;
+        const int s = h->s;
+        const long long item = (long long)s * g.nx;
+        const unsigned nbr = blocks_for_rows(g.R);
+        if (!transpose) {
+            launch(k_schur_rhs<A>, nbr, kBlock, 0, st(), g, s, (const StepPtrs*)stepp, tbuf, facesA);
+            AAO_TRY(inner<A>(1, tbuf, item, nullptr, 0, 0));
+            launch(k_schur_update<SI, A>, nbr, kBlock, 0, st(), g, s, (const A*)wbuf, (const StepPtrs*)stepp, Z0,
+                   zstride, (const double*)yh, kin, (const int*)itsh, (const double*)h->d_b, h->tau);
+            launch(k_step_add, 1, 1, 0, st(), stepp, 1);
+        } else {
+            launch(k_schurT_rhs<A>, (unsigned)((item + 255) / 256), 256, 0, st(), g.nx, s, (const StepPtrs*)stepp,
+                   (const double*)h->d_b, tbuf);
+            AAO_TRY(inner<A>(1, tbuf, item, nullptr, 0, 1));
+            Vec<SI> Zc = Z0;
+            launch(k_combine<SI, A>, blocks_for_rows((long long)s * g.R), kBlock, 0, st(), g.n0, (long long)s * g.R, 1,
+                   Zc, zstride, (const double*)yh, kin, (const int*)itsh, qbuf, item, 0);
+            launch(k_schurT_update<A>, nbr, kBlock, 0, st(), g, s, (const StepPtrs*)stepp, (const A*)qbuf, h->tau,
+                   facesA);
+            launch(k_step_add, 1, 1, 0, st(), stepp, -1);
+        }
+        AAO_LAUNCH_CHECK();
+        return AAO_OK;
+    }
+
+    // Capture one step into a CUDA graph (on a private stream) the first time
+    // it is needed; replays then issue the whole step with one launch.
+    aao_status ensure_graph(int transpose) {
+        if (gexec[transpose]) return AAO_OK;
+        if (!cap_stream) AAO_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+        cudaStream_t keep = cur_stream;
+        cur_stream = cap_stream;
+        long long before = g_launches;
+        AAO_CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+        aao_status st_ = schur_step(transpose);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
+        cur_stream = keep;
+        g_launches = before;
+        if (st_ != AAO_OK) return st_;
+        if (e != cudaSuccess) {
+            set_error(std::string("graph capture failed: ") + cudaGetErrorString(e));
+            return AAO_ERR_CUDA;
+        }
+        size_t nodes = 0;
+        cudaGraphGetNodes(graph, nullptr, &nodes);
+        graph_nodes[transpose] = (long long)nodes;
+        e = cudaGraphInstantiate(&gexec[transpose], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            gexec[transpose] = nullptr;
+            set_error(std::string("graph instantiation failed: ") + cudaGetErrorString(e));
+            return AAO_ERR_CUDA;
+        }
+        return AAO_OK;
+    }
+
+    aao_status schur_sweep(int transpose) {
+        const int nt = h->nt;
+        // launch profiles need one event pair per kernel: run eagerly then
+        const bool use_graph = !g_prof_on;
+        if (use_graph) AAO_TRY(ensure_graph(transpose));
+        for (int q = 0; q < nt; ++q) {
+            if (use_graph) {
+                AAO_CUDA_TRY(cudaGraphLaunch(gexec[transpose], st()));
+                g_launches += graph_nodes[transpose];
+            } else {
+                AAO_TRY(schur_step(transpose));
+            }
+        }
+        return AAO_OK;
+    }
+
     aao_status apply(const double* r, double* z, int transpose) override {
         const Geo& g = h->g;
         const int s = h->s, nt = h->nt;
         const long long nx = g.nx, nv = h->nv, item = (long long)s * nx;
-        const unsigned nbr = blocks_for_rows(g.R);
         cudaEventRecord(e0, st());
         if (!transpose) {
             AAO_TRY(inner<double>(nt, r + nv, item, z + nv, item, 0));
             cudaEventRecord(e1, st());
             long long tot = (nt + 1) * nx;
-            launch(k_schur_g<A>, (unsigned)((tot + 255) / 256), 256, 0, st(), nx, nt, s, r, z + nv, h->d_b, h->tau, wbuf,
-                                                                          z);
+            launch(k_schur_g<A>, (unsigned)((tot + 255) / 256), 256, 0, st(), nx, nt, s, r, (const double*)(z + nv),
+                   (const double*)h->d_b, h->tau, wbuf, z);
+            launch(k_step_set, 1, 1, 0, st(), stepp, z, r, 0);
             AAO_LAUNCH_CHECK();
-            for (int n = 0; n < nt; ++n) {
-                launch(k_schur_rhs<A>, nbr, kBlock, 0, st(), g, s, z + n * nx, tbuf, facesA);
-                AAO_TRY(inner<A>(1, tbuf, item, nullptr, 0, 0));
-                launch(k_schur_update<SI, A>, nbr, kBlock, 0, st(), g, s, wbuf + (n + 1) * nx, z + n * nx, Z0, zstride,
-                                                                yh, kin, itsh, h->d_b, h->tau, z + (n + 1) * nx);
-                AAO_LAUNCH_CHECK();
-            }
+            AAO_TRY(schur_sweep(0));
             cudaEventRecord(e2, st());
         } else {
             // S_tilde^T: backward substitution, u stored in z's v-part (M = I: z_v = u)
             AAO_CUDA_TRY(cudaMemcpyAsync(z + nt * nx, r + nt * nx, sizeof(double) * nx, cudaMemcpyDeviceToDevice,
                                          st()));
-            const unsigned nbt = (unsigned)((item + 255) / 256);
-            for (int n = nt - 1; n >= 0; --n) {
-                launch(k_schurT_rhs<A>, nbt, 256, 0, st(), nx, s, z + (n + 1) * nx, h->d_b, tbuf);
-                AAO_TRY(inner<A>(1, tbuf, item, nullptr, 0, 1));
-                Vec<SI> Zc = Z0;
-                launch(k_combine<SI, A>, blocks_for_rows((long long)s * g.R), kBlock, 0, st(), 
-                    g.n0, (long long)s * g.R, 1, Zc, zstride, yh, kin, itsh, qbuf, item, 0);
-                launch(k_schurT_update<A>, nbr, kBlock, 0, st(), g, s, r + n * nx, z + (n + 1) * nx, qbuf, h->tau, facesA,
-                                                             z + n * nx);
-                AAO_LAUNCH_CHECK();
-            }
+            launch(k_step_set, 1, 1, 0, st(), stepp, z, r, nt - 1);
+            AAO_LAUNCH_CHECK();
+            AAO_TRY(schur_sweep(1));
             cudaEventRecord(e1, st());
             long long tot = (long long)nt * item;
-            launch(k_schurT_vrhs<A>, (unsigned)((tot + 255) / 256), 256, 0, st(), nx, nt, s, r + nv, z, h->d_b, h->tau, tV);
+            launch(k_schurT_vrhs<A>, (unsigned)((tot + 255) / 256), 256, 0, st(), nx, nt, s, r + nv, (const double*)z,
+                   (const double*)h->d_b, h->tau, tV);
             AAO_LAUNCH_CHECK();
             AAO_TRY(inner<A>(nt, tV, item, z + nv, item, 1));
             cudaEventRecord(e2, st());
@@ -477,6 +625,7 @@ class Precond : public PrecondBase {
     // ------------------------------------------------- component entry points
     aao_status shifted_solve(int stage, const double* b, double* x) override {
         const Geo& g = h->g;
+        nact = 1;
         launch(k_scale_store<SI, double>, blocks_for_rows(g.R), kBlock, 0, st(), g.n0, g.R, 1, nullptr, b, g.nx,
                                                                              nullptr, 0, mgb);
         AAO_LAUNCH_CHECK();
@@ -489,6 +638,7 @@ class Precond : public PrecondBase {
 
     aao_status pint_apply(const double* r, double* y, int transpose) override {
         const Geo& g = h->g;
+        nact = 1;
         const long long rows = (long long)h->s * g.R;
         launch(k_scale_store<SP, double>, blocks_for_rows(rows), kBlock, 0, st(), g.n0, rows, 1, nullptr, r,
                                                                               (long long)h->s * g.nx, nullptr, 0, V0);

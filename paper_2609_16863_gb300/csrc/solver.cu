@@ -4,13 +4,57 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 
 #include "handle.cuh"
 
 namespace aao {
 
 long long g_launches = 0;
+bool g_prof_on = false;
+thread_local double g_bytes_hint = 0.0;
 static thread_local std::string g_last_error;
+
+// ---- launch profiling: events around launches of kernels matching a name
+struct ProfState {
+    std::string match;
+    std::unordered_map<const void*, bool> hit;
+    std::vector<cudaEvent_t> ev;      // pool, pairs
+    std::vector<double> bytes;
+    size_t used = 0;
+    std::string first_name;
+};
+static ProfState g_prof;
+
+int prof_begin_launch(const void* k, cudaStream_t st, double bytes) {
+    auto it = g_prof.hit.find(k);
+    bool h;
+    if (it == g_prof.hit.end()) {
+        const char* name = nullptr;
+        h = cudaFuncGetName(&name, k) == cudaSuccess && name && std::strstr(name, g_prof.match.c_str());
+        if (h && g_prof.first_name.empty()) g_prof.first_name = name;
+        cudaGetLastError();
+        g_prof.hit[k] = h;
+    } else {
+        h = it->second;
+    }
+    if (!h) return -1;
+    if (g_prof.used * 2 + 2 > g_prof.ev.size()) {
+        if (g_prof.ev.size() >= 4000000) return -1;
+        size_t add = g_prof.ev.size() ? g_prof.ev.size() : 4096;
+        for (size_t i = 0; i < add; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            g_prof.ev.push_back(e);
+        }
+    }
+    int slot = (int)g_prof.used++;
+    g_prof.bytes.push_back(bytes);
+    cudaEventRecord(g_prof.ev[2 * slot], st);
+    return slot;
+}
+
+void prof_end_launch(int slot, cudaStream_t st) { cudaEventRecord(g_prof.ev[2 * slot + 1], st); }
 void set_error(const std::string& msg) { g_last_error = msg; }
 const char* get_error() { return g_last_error.c_str(); }
 
@@ -321,6 +365,7 @@ static aao_status setup_handle(Handle* h, const aao_grid* grid, double tau, int 
 // ---------------------------------------------------------------------------
 static aao_status matvec_dev(Handle* h, const double* x, double* y, const double* rhs, int transpose) {
     const Geo& g = h->g;
+    bytes_hint(8.0 * h->nst * (rhs ? 3 : 2));
     launch(k_matvec, blocks_for_rows((long long)(h->nt + 1) * g.R), kBlock, 0, h->stream, 
         g, h->nt, h->tab, h->tau, h->faces64, x, y, rhs, transpose);
     AAO_LAUNCH_CHECK();
@@ -540,6 +585,38 @@ void aao_rk_default_options(aao_options* o) {
 const char* aao_rk_last_error(void) { return get_error(); }
 
 long long aao_rk_launch_count(void) { return g_launches; }
+
+aao_status aao_rk_profile_begin(const char* kernel_name) {
+    if (!kernel_name || !*kernel_name) {
+        set_error("empty kernel name");
+        return AAO_ERR_ARG;
+    }
+    g_prof.match = kernel_name;
+    g_prof.hit.clear();
+    g_prof.bytes.clear();
+    g_prof.used = 0;
+    g_prof.first_name.clear();
+    g_prof_on = true;
+    return AAO_OK;
+}
+
+aao_status aao_rk_profile_end(long long* launches, double* total_ms, double* total_bytes) {
+    g_prof_on = false;
+    AAO_CUDA_TRY(cudaDeviceSynchronize());
+    double ms = 0.0, by = 0.0;
+    for (size_t i = 0; i < g_prof.used; ++i) {
+        float t = 0.f;
+        AAO_CUDA_TRY(cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]));
+        ms += t;
+        by += g_prof.bytes[i];
+    }
+    if (launches) *launches = (long long)g_prof.used;
+    if (total_ms) *total_ms = ms;
+    if (total_bytes) *total_bytes = by;
+    g_prof.used = 0;
+    g_prof.bytes.clear();
+    return AAO_OK;
+}
 
 aao_status aao_rk_setup(const aao_grid* grid, double tau, int nt, const aao_tableau* tab, const aao_options* opts,
                         aao_rk_handle* out) {

@@ -1,0 +1,133 @@
+"""GPU adjoint path vs the FP64 oracle and against central finite differences."""
+import numpy as np
+import pytest
+
+import synth
+from oracle.adjoint import adjoint_solve, grad_f, grad_kappa, tracking_dJdx
+from oracle.solve import OracleOptions, build, solve as oracle_solve
+
+from gpu_util import dev, host, rel_max, to_dev, torch, zeros
+
+pytestmark = pytest.mark.gpu
+
+KW = dict(inner_maxit=3, inner_tol=1e-6, mg_cycles=3, mg_pre=2, mg_post=2, mg_omega=0.8)
+
+
+def solver(ns, nt, s, kap, prec="fp64", tol=1e-12, T=0.5):
+    from paper_2609_16863_gb300 import Solver, radau_iia
+    dev()
+    return Solver(ns, T, nt, tableau=radau_iia(s), kappa=None if kap is None else to_dev(kap), prec_P=prec,
+                  tol=tol, **KW)
+
+
+def data(ns, seed=9):
+    kap = np.exp(synth.gaussian_random_field(ns, 0.15, 0.5, synth.rng_for(seed, "kappa"), with_boundary=True))
+    u0 = synth.gaussian_random_field(ns, 0.2, 1.0, synth.rng_for(seed, "u0"))
+    f = synth.gaussian_random_field(ns, 0.2, 1.0, synth.rng_for(seed, "f"))
+    tgt = synth.gaussian_random_field(ns, 0.2, 1.0, synth.rng_for(seed, "target"))
+    return kap, u0, f, tgt
+
+
+def test_dot_product_identity():
+    ns, nt, s = (20, 18), 4, 3
+    kap, *_ = data(ns)
+    S = solver(ns, nt, s, kap)
+    x = to_dev(synth.random_vector(S.n_st, 1))
+    y = to_dev(synth.random_vector(S.n_st, 2))
+    Ax = S.matvec(x, zeros(S.n_st))
+    ATy = S.matvec(y, zeros(S.n_st), transpose=True)
+    a = float(torch.dot(Ax, y))
+    b = float(torch.dot(x, ATy))
+    assert abs(a - b) <= 1e-13 * abs(a)
+
+
+@pytest.mark.parametrize("ns,nt,s", [((16, 14), 4, 3), ((8, 7, 9), 3, 2)])
+def test_adjoint_solve_and_gradients_match_oracle(ns, nt, s):
+    kap, u0, f, tgt = data(ns)
+    S = solver(ns, nt, s, kap)
+    x = host(S.solve(to_dev(f), to_dev(u0), zeros(S.n_st))[0])
+    op = build(ns, 0.5, nt, "radau", s, kappa=kap)
+    g = tracking_dJdx(op, x, tgt)
+    lam_d = zeros(S.n_st)
+    gf_d = zeros(S.nx)
+    nnode = int(np.prod([n + 2 for n in ns]))
+    gk_d = zeros(nnode)
+    _, info = S.adjoint_solve(to_dev(g), lam_d, x_fwd=to_dev(x), grad_f=gf_d, grad_kappa=gk_d)
+    lam = host(lam_d)
+    ref, its, rr, ok = adjoint_solve(op, ns, g, tol=1e-12, inner_maxit=3, inner_tol=1e-6, omega=0.8)
+    assert info.converged and ok and info.outer_its == its
+    assert np.linalg.norm(lam - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert rel_max(host(gf_d), grad_f(op, lam)) <= 1e-12
+    assert rel_max(host(gk_d), grad_kappa(op, ns, lam, x)) <= 1e-11
+
+
+def _J(S, f, u0, tgt):
+    x = S.solve(to_dev(f), to_dev(u0), zeros(S.n_st))[0]
+    xh = host(x)
+    lo = S.nt * S.nx
+    d = xh[lo: lo + S.nx] - tgt
+    return 0.5 * d @ d + 0.5e-4 * f @ f
+
+
+def test_gradients_against_central_differences():
+    """h = 1e-6, forward solves to 1e-13 so solver noise stays far below the 1e-5 target."""
+    ns, nt, s = (12, 12), 4, 3
+    kap, u0, f, tgt = data(ns, seed=4)
+    S = solver(ns, nt, s, kap, tol=1e-13)
+    x = host(S.solve(to_dev(f), to_dev(u0), zeros(S.n_st))[0])
+    op = build(ns, 0.5, nt, "radau", s, kappa=kap)
+    gf_d = zeros(S.nx)
+    gk_d = zeros(kap.size)
+    S.adjoint_solve(to_dev(tracking_dJdx(op, x, tgt)), zeros(S.n_st), x_fwd=to_dev(x), grad_f=gf_d,
+                    grad_kappa=gk_d)
+    gf = host(gf_d) + 1e-4 * f
+    gk = host(gk_d)
+    h = 1e-6
+    D = synth.fd_directions(f.size, 3, seed=5)
+    for d in D:
+        fd = (_J(S, f + h * d, u0, tgt) - _J(S, f - h * d, u0, tgt)) / (2 * h)
+        assert abs(fd - gf @ d) <= 1e-5 * max(1.0, abs(fd))
+    Dk = synth.fd_directions(kap.size, 3, seed=6)
+    for d in Dk:
+        Sp = solver(ns, nt, s, kap + h * d, tol=1e-13)
+        Sm = solver(ns, nt, s, kap - h * d, tol=1e-13)
+        fd = (_J(Sp, f, u0, tgt) - _J(Sm, f, u0, tgt)) / (2 * h)
+        assert abs(fd - gk @ d) <= 1e-5 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mixed_precision_adjoint_gradient(prec):
+    ns, nt, s = (24, 24), 4, 3
+    kap, u0, f, tgt = data(ns, seed=7)
+    S64 = solver(ns, nt, s, kap)
+    x = host(S64.solve(to_dev(f), to_dev(u0), zeros(S64.n_st))[0])
+    op = build(ns, 0.5, nt, "radau", s, kappa=kap)
+    g = to_dev(tracking_dJdx(op, x, tgt))
+    out = {}
+    for p, S in (("fp64", S64), (prec, solver(ns, nt, s, kap, prec=prec, tol=1e-12))):
+        gk = zeros(kap.size)
+        S.adjoint_solve(g, zeros(S.n_st), x_fwd=to_dev(x), grad_kappa=gk)
+        out[p] = host(gk)
+    err = np.linalg.norm(out[prec] - out["fp64"]) / np.linalg.norm(out["fp64"])
+    assert err <= 1e-9, err
+
+
+def test_autograd_function():
+    from paper_2609_16863_gb300.autograd import heat_solve
+    from paper_2609_16863_gb300 import radau_iia
+    ns, nt, s = (10, 9), 3, 2
+    kap, u0, f, tgt = data(ns, seed=11)
+    cfg = dict(n=ns, T=0.5, nt=nt, tableau=radau_iia(s), prec_P="fp64", tol=1e-13, **KW)
+    fd_ = to_dev(f).requires_grad_(True)
+    ud = to_dev(u0).requires_grad_(True)
+    kd = to_dev(kap).requires_grad_(True)
+    x = heat_solve(fd_, ud, kd, **cfg)
+    lo = nt * int(np.prod(ns))
+    J = 0.5 * ((x[lo: lo + f.size] - to_dev(tgt)) ** 2).sum() + 0.5e-4 * (fd_ ** 2).sum()
+    J.backward()
+    op = build(ns, 0.5, nt, "radau", s, kappa=kap)
+    xr = np.linalg.solve(op.dense(), op.rhs(u0, f))
+    lam = np.linalg.solve(op.dense().T, tracking_dJdx(op, xr, tgt))
+    assert rel_max(host(fd_.grad), grad_f(op, lam) + 1e-4 * f) <= 1e-9
+    assert rel_max(host(ud.grad), lam[: f.size]) <= 1e-9
+    assert rel_max(host(kd.grad), grad_kappa(op, ns, lam, xr)) <= 1e-9
