@@ -193,6 +193,26 @@ aao_status aao_rk_pint_apply(aao_rk_handle h, const double* r, double* y, int tr
  * (inner GMRES); its (may be NULL) receives the iterations per block. */
 aao_status aao_rk_inner_solve(aao_rk_handle h, int nblocks, const double* r, double* z, int* its);
 
+/* ---- allocation-free variant (no counterpart in the paper) ----
+ *
+ * x ~= (I + c K)^{-1} b on the constant-coefficient FD grid `grid` by `cycles`
+ * V(pre, post)-cycles with Jacobi weight omega, the same multigrid as the
+ * handle's shifted solves, computed in FP64.  For callers that cannot allocate
+ * device memory (pools that forbid cudaMalloc, hosts that only hand out
+ * pre-registered buffers, code that must not allocate after start-up): it
+ * needs no handle and calls no allocating routine.  All scratch lives in one
+ * fixed 5 MiB device array inside the library, which every GPU that loads the
+ * library keeps until the process exits; grids above 65536 points (or whose
+ * coarsest level exceeds 64 points) are rejected with AAO_ERR_ARG.  b and x
+ * are device memory (n_x values, host pointers are rejected), the work is
+ * queued on `stream` (NULL = default stream).  The first call on a device looks
+ * up the array's device address, so make it before any stream capture.  Every
+ * call reuses the same array: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  The scratch keeps
+ * the last call's contents; each call rebuilds what it reads. */
+aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double c, int cycles, int pre, int post,
+                                        double omega, const double* b, double* x, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

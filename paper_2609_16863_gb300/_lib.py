@@ -71,6 +71,8 @@ SIGNATURES = [
     ("aao_rk_shifted_solve", C.c_int, [H, C.c_int, P, P]),
     ("aao_rk_pint_apply", C.c_int, [H, P, P, C.c_int]),
     ("aao_rk_inner_solve", C.c_int, [H, C.c_int, P, P, C.POINTER(C.c_int)]),
+    ("aao_rk_shifted_solve_noalloc", C.c_int, [C.POINTER(aao_grid), C.c_double, C.c_int, C.c_int, C.c_int,
+                                               C.c_double, P, P, C.c_void_p]),
 ]
 
 
