@@ -132,6 +132,10 @@ long long aao_rk_launch_count(void);
  * summed event time and their summed algorithmic bytes. */
 aao_status aao_rk_profile_begin(const char* kernel_name);
 aao_status aao_rk_profile_end(long long* launches, double* total_ms, double* total_bytes);
+/* Per-kernel breakdown of the last completed profile, one line per kernel:
+ * "<mangled name>\t<launches>\t<event ms>\t<algorithmic bytes>\n".  The text stays
+ * valid until the next aao_rk_profile_end. */
+const char* aao_rk_profile_report(void);
 
 /* n_x = prod(n), n_st = n_x (nt + 1 + s nt). */
 aao_status aao_rk_sizes(aao_rk_handle h, long long* n_x, long long* n_st);

@@ -56,6 +56,7 @@ SIGNATURES = [
     ("aao_rk_launch_count", C.c_longlong, []),
     ("aao_rk_profile_begin", C.c_int, [C.c_char_p]),
     ("aao_rk_profile_end", C.c_int, [C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("aao_rk_profile_report", C.c_char_p, []),
     ("aao_rk_sizes", C.c_int, [H, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     ("aao_rk_set_options", C.c_int, [H, C.POINTER(aao_options)]),
     ("aao_rk_rhs", C.c_int, [H, P, C.c_int, P, P]),

@@ -7,6 +7,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cmath>
 #include <string>
 
@@ -24,6 +25,7 @@ constexpr int kMaxInner = 16;            // inner GMRES iterations
 constexpr int kMaxRestart = 64;          // outer FGMRES restart
 constexpr int kMaxLevels = 16;
 constexpr int kMaxCoarsest = 512;        // unknowns of the dense coarsest solve
+constexpr int kPtMaxThreads = 512;       // threads per CTA of the point-mapped row kernels
 
 // ---------------------------------------------------------------------------
 // Storage precision traits.  Arithmetic is double for FP64 storage and float
@@ -134,6 +136,79 @@ __device__ __forceinline__ void row_store(S* out, float* out_sc, int n0, int lan
     }
 }
 
+// ---------------------------------------------------------------------------
+// Point mapping of the row kernels.  A CTA of rpc * n0p threads covers rpc
+// whole grid rows (n0p = n0 rounded up to a warp multiple, at most 512);
+// thread (lrow, c0) computes columns c0, c0 + n0p, ... of its row.  Because a
+// CTA holds whole rows, the per-row scale of a 16-bit row is a CTA-local
+// reduction.
+// ---------------------------------------------------------------------------
+struct PtMap {
+    int n0, n0p, rpc;
+};
+
+inline PtMap ptmap(int n0) {
+    PtMap m;
+    m.n0 = n0;
+    int p = (n0 + kWarp - 1) / kWarp * kWarp;
+    if (p > kPtMaxThreads) p = kPtMaxThreads;
+    m.n0p = p;
+    m.rpc = p >= 256 ? 1 : 256 / p;
+    return m;
+}
+inline unsigned int pt_blocks(const PtMap& m, long long rows) {
+    long long b = (rows + m.rpc - 1) / m.rpc;
+    return (unsigned int)(b < 1 ? 1 : b);
+}
+inline unsigned int pt_threads(const PtMap& m) { return (unsigned int)(m.rpc * m.n0p); }
+
+// Row coordinates of the calling thread for B items of R rows each.
+struct PtPos {
+    int lrow, c0, b;
+    long long row;
+    bool valid;
+};
+__device__ __forceinline__ PtPos pt_pos(const PtMap& m, int B, int R, const int* active) {
+    PtPos q;
+    q.lrow = threadIdx.x / m.n0p;
+    q.c0 = threadIdx.x % m.n0p;
+    long long w = (long long)blockIdx.x * m.rpc + q.lrow;
+    q.valid = w < (long long)B * R;
+    q.b = q.valid ? (int)(w / R) : 0;
+    q.row = q.valid ? w % R : 0;
+    if (q.valid && active && !active[q.b]) q.valid = false;
+    return q;
+}
+
+// Store f(c) for this thread's columns of one row (scaled types: n0 <= n0p, one
+// column per thread).  Every thread of the CTA must call it for scaled types.
+template <class S, class F>
+__device__ __forceinline__ void pt_store(S* out_row, float* out_sc, const PtMap& m, int c0, bool valid, F&& f) {
+    if constexpr (PT<S>::scaled) {
+        __shared__ float wmax[32];
+        float v = 0.f;
+        if (valid && c0 < m.n0) v = (float)f(c0);
+        float a = warp_max(fabsf(v));
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = a;
+        __syncthreads();
+        const int wpr = m.n0p >> 5, first = (threadIdx.x / m.n0p) * wpr;
+        float mx = 0.f;
+        for (int i = 0; i < wpr; ++i) mx = fmaxf(mx, wmax[first + i]);
+        int e = 0;
+        float sc = 1.f, inv = 1.f;
+        if (mx > 0.f && mx <= 3.0e38f) {
+            frexpf(mx, &e);
+            sc = ldexpf(1.f, e - 14);
+            inv = ldexpf(1.f, 14 - e);
+        }
+        if (valid && c0 < m.n0) out_row[c0] = PT<S>::st(v * inv);
+        if (valid && c0 == 0) *out_sc = sc;
+    } else {
+        if (valid)
+            for (int c = c0; c < m.n0; c += m.n0p) out_row[c] = PT<S>::st((typename PT<S>::A)f(c));
+    }
+}
+
 template <class S>
 __device__ __forceinline__ void row_store_ptrs(const Vec<S>& v, long long b, long long elem_off,
                                                long long row, int n0, S*& out, float*& out_sc) {
@@ -215,6 +290,12 @@ __device__ __forceinline__ A fd_K_diag(const Geo& g, const Faces<T>& f, long lon
     return dg;
 }
 
+// First statement of every kernel of the library (see launch()).
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Global warp id and lane for row kernels.
 __device__ __forceinline__ long long gwarp() {
     return ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -226,19 +307,38 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 // When a profile is open (aao_rk_profile_begin), launches of kernels whose name
 // contains the requested text are bracketed by CUDA events on their stream and
 // credited with the algorithmic bytes the launch site declared by bytes_hint().
-extern long long g_launches;
+extern std::atomic<long long> g_launches;
+extern thread_local long long g_thread_launches;   // launches issued by this host thread
 extern bool g_prof_on;
 extern thread_local double g_bytes_hint;
 int prof_begin_launch(const void* k, cudaStream_t st, double bytes);
 void prof_end_launch(int slot, cudaStream_t st);
 inline void bytes_hint(double b) { g_bytes_hint = b; }
+//
+// Kernels are launched with programmatic stream serialisation (programmatic
+// dependent launch): a kernel may be scheduled while its predecessor on the
+// stream is still running, so every kernel starts with pdl_prologue(), which
+// waits for the predecessor grid to complete (and its writes to be visible)
+// before anything else, then allows its own successor to start launching.
+// Stream order is therefore unchanged; only launch latency is overlapped.
 template <class... KArgs, class... Args>
 inline void launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t shmem, cudaStream_t st, Args... args) {
     ++g_launches;
+    ++g_thread_launches;
     double bytes = g_bytes_hint;
     g_bytes_hint = 0.0;
     int slot = g_prof_on ? prof_begin_launch((const void*)k, st, bytes) : -1;
-    k<<<grid, block, shmem, st>>>(args...);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = shmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
     if (slot >= 0) prof_end_launch(slot, st);
 }
 

@@ -111,9 +111,11 @@ struct Handle {
     cudaEvent_t ev[4];
     int ev_ok = 0;
 
-    int nchunk_for(int B, long long rows) const {
+    // reduction blocks per item: about 8 blocks per SM over the whole batch, at
+    // most one 32-column segment per warp
+    int nchunk_for(int B, long long segments) const {
         long long target = (152LL * 8 + B - 1) / B;
-        long long maxc = (rows + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        long long maxc = (segments + kWarpsPerBlock - 1) / kWarpsPerBlock;
         long long c = target < maxc ? target : maxc;
         if (c > red_cap_chunks) c = red_cap_chunks;
         return (int)(c < 1 ? 1 : c);

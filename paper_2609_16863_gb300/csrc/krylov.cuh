@@ -51,21 +51,29 @@ __device__ __forceinline__ void block_finish(double v, int b, const Red& red, do
     }
 }
 
-// ||src_b|| for an unscaled source (double or float), rows of n0.
+// ||src_b|| for an unscaled source (double or float), rows of n0.  Work is
+// split in 32-column segments (one per warp iteration) so that a single item
+// still spreads over many warps.
 template <class SR>
 __global__ void __launch_bounds__(kBlock) k_norm(int n0, long long rows, int B, const int* active,
                                                  const SR* src, long long bs, Red red, double* out,
                                                  long long ostride) {
+    pdl_prologue();
     int b = blockIdx.y;
     if (active && !active[b]) return;
     const SR* x = src + (long long)b * bs;
-    int w = threadIdx.x >> 5, lane = lane_id();
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    const int spr = (n0 + kWarp - 1) / kWarp;
+    const long long nseg = rows * spr;
     SR acc = SR(0);
-    for (long long r = (long long)blockIdx.x * kWarpsPerBlock + w; r < rows; r += (long long)red.nchunk * kWarpsPerBlock)
-        for (int c = lane; c < n0; c += kWarp) {
+    for (long long g = (long long)blockIdx.x * kWarpsPerBlock + w; g < nseg; g += (long long)red.nchunk * kWarpsPerBlock) {
+        long long r = g / spr;
+        int c = (int)(g % spr) * kWarp + lane;
+        if (c < n0) {
             SR v = x[r * n0 + c];
             acc += v * v;
         }
+    }
     block_finish((double)acc, b, red, out + (long long)b * ostride, 1);
 }
 
@@ -75,6 +83,7 @@ template <class SV, class A>
 __global__ void __launch_bounds__(kBlock) k_mgs(int n0, long long rows, int B, const int* active, A* wv,
                                                 long long wbs, Vec<SV> Vp, const double* hp, Vec<SV> Vn,
                                                 long long hstride, Red red, double* out) {
+    pdl_prologue();
     int b = blockIdx.y;
     if (active && !active[b]) return;
     A* w = wv + (long long)b * wbs;
@@ -82,10 +91,14 @@ __global__ void __launch_bounds__(kBlock) k_mgs(int n0, long long rows, int B, c
     View<SV> vp = upd ? view_of(Vp, b, 0, n0) : View<SV>{nullptr, nullptr, n0};
     View<SV> vn = dot ? view_of(Vn, b, 0, n0) : View<SV>{nullptr, nullptr, n0};
     A h = upd ? (A)hp[(long long)b * hstride] : A(0);
-    int wi = threadIdx.x >> 5, lane = lane_id();
+    const int wi = threadIdx.x >> 5, lane = lane_id();
+    const int spr = (n0 + kWarp - 1) / kWarp;
+    const long long nseg = rows * spr;
     A acc = A(0);
-    for (long long r = (long long)blockIdx.x * kWarpsPerBlock + wi; r < rows; r += (long long)red.nchunk * kWarpsPerBlock)
-        for (int c = lane; c < n0; c += kWarp) {
+    for (long long g = (long long)blockIdx.x * kWarpsPerBlock + wi; g < nseg; g += (long long)red.nchunk * kWarpsPerBlock) {
+        long long r = g / spr;
+        int c = (int)(g % spr) * kWarp + lane;
+        if (c < n0) {
             long long i = r * n0 + c;
             A x = w[i];
             if (upd) {
@@ -94,37 +107,39 @@ __global__ void __launch_bounds__(kBlock) k_mgs(int n0, long long rows, int B, c
             }
             acc += dot ? vn.at(r, c) * x : x * x;
         }
+    }
     block_finish((double)acc, b, red, out + (long long)b * hstride, dot ? 0 : 1);
 }
 
-// out_b = src_b / denom[b * dstride]  (row store, any storage); inactive items skipped.
+// out_b = src_b / denom[b * dstride]  (any storage); inactive items skipped.
 template <class SO, class SR>
-__global__ void __launch_bounds__(kBlock) k_scale_store(int n0, long long rows, int B, const int* active,
-                                                        const SR* src, long long sbs, const double* denom,
-                                                        long long dstride, Vec<SO> out) {
-    long long w = gwarp();
-    if (w >= (long long)B * rows) return;
-    int b = (int)(w / rows);
-    long long row = w % rows;
-    if (active && !active[b]) return;
+__global__ void __launch_bounds__(kPtMaxThreads) k_scale_store(PtMap pm, int rows, int B, const int* active, const SR* src,
+                                                      long long sbs, const double* denom, long long dstride,
+                                                      Vec<SO> out) {
+    pdl_prologue();
     using A = typename PT<SO>::A;
-    const SR* x = src + (long long)b * sbs + row * n0;
-    A inv = denom ? A(1.0 / denom[(long long)b * dstride]) : A(1);
+    PtPos q = pt_pos(pm, B, rows, active);
+    if constexpr (!PT<SO>::scaled) {
+        if (!q.valid) return;
+    }
+    const int n0 = pm.n0;
+    const SR* x = src + (long long)q.b * sbs + q.row * n0;
+    A inv = (denom && q.valid) ? A(1.0 / denom[(long long)q.b * dstride]) : A(1);
     SO* o; float* osc;
-    row_store_ptrs(out, b, 0, row, n0, o, osc);
-    row_store<SO>(o, osc, n0, lane_id(), [&](int c) -> A { return A(x[c]) * inv; });
+    row_store_ptrs(out, q.b, 0, q.row, n0, o, osc);
+    pt_store<SO>(o, osc, pm, q.c0, q.valid, [&](int c) -> A { return A(x[c]) * inv; });
 }
 
 // Read a stored vector back into an unscaled array.
 template <class S, class SO>
-__global__ void __launch_bounds__(kBlock) k_load(int n0, long long rows, int B, Vec<S> in, SO* out, long long obs) {
-    long long w = gwarp();
-    if (w >= (long long)B * rows) return;
-    int b = (int)(w / rows);
-    long long row = w % rows;
-    View<S> v = view_of(in, b, 0, n0);
-    SO* o = out + (long long)b * obs + row * n0;
-    for (int c = lane_id(); c < n0; c += kWarp) o[c] = (SO)v.at(row, c);
+__global__ void __launch_bounds__(kPtMaxThreads) k_load(PtMap pm, int rows, int B, Vec<S> in, SO* out, long long obs) {
+    pdl_prologue();
+    PtPos q = pt_pos(pm, B, rows, nullptr);
+    if (!q.valid) return;
+    const int n0 = pm.n0;
+    View<S> v = view_of(in, q.b, 0, n0);
+    SO* o = out + (long long)q.b * obs + q.row * n0;
+    for (int c = q.c0; c < n0; c += pm.n0p) o[c] = (SO)v.at(q.row, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -135,6 +150,7 @@ __global__ void __launch_bounds__(kBlock) k_load(int n0, long long rows, int B, 
 static __global__ void k_givens(int B, int k, int kmax, double* H, long long hs, double* cs, double* sn, double* g,
                          const double* beta_ref, double tol, int* active, int* its, int* nonfinite,
                          double* resid_out) {
+    pdl_prologue();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B || !active[b]) return;
     double* h = H + (long long)b * hs;
@@ -173,6 +189,7 @@ static __global__ void k_givens(int B, int k, int kmax, double* H, long long hs,
 
 // Start of a batched inner solve: items with beta == 0 are done at once (z = 0).
 static __global__ void k_inner_init(int B, int kmax, const double* beta, int* active, int* its, double* g, int* nonfinite) {
+    pdl_prologue();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     double bt = beta[b];
@@ -183,6 +200,7 @@ static __global__ void k_inner_init(int B, int kmax, const double* beta, int* ac
 }
 
 static __global__ void k_count_its(int B, const int* its, long long* count) {
+    pdl_prologue();
     __shared__ long long sh[128];
     long long t = 0;
     for (int b = threadIdx.x; b < B; b += blockDim.x) t += its[b];
@@ -198,6 +216,7 @@ static __global__ void k_count_its(int B, const int* its, long long* count) {
 // y = R^{-1} g (R the rotated upper triangle, its[b] columns), per item.
 static __global__ void k_hess_solve(int B, int kmax, const double* H, long long hs, const double* g, const int* its,
                              double* y, int* breakdown) {
+    pdl_prologue();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     const double* h = H + (long long)b * hs;
@@ -220,26 +239,24 @@ static __global__ void k_hess_solve(int B, int kmax, const double* H, long long 
 
 // out_b (+)= sum_{k < its[b]} y[b][k] Z_k,b ; Z_k at Z0 shifted by k*zstride elements.
 template <class SZ, class SO>
-__global__ void __launch_bounds__(kBlock) k_combine(int n0, long long rows, int B, Vec<SZ> Z0, long long zstride,
-                                                    const double* y, int kmax, const int* its, SO* out,
-                                                    long long obs, int accumulate) {
-    long long w = gwarp();
-    if (w >= (long long)B * rows) return;
-    int b = (int)(w / rows);
-    long long row = w % rows;
+__global__ void __launch_bounds__(kPtMaxThreads) k_combine(PtMap pm, int rows, int B, Vec<SZ> Z0, long long zstride,
+                                                  const double* y, int kmax, const int* its, SO* out, long long obs,
+                                                  int accumulate) {
+    pdl_prologue();
+    PtPos q = pt_pos(pm, B, rows, nullptr);
+    if (!q.valid) return;
     using A = typename PT<SZ>::A;
-    int m = its ? its[b] : kmax;
-    A yk[kMaxRestart];
-    for (int k = 0; k < m; ++k) yk[k] = (A)y[(long long)b * kmax + k];
-    SO* o = out + (long long)b * obs + row * n0;
-    for (int c = lane_id(); c < n0; c += kWarp) {
+    const int n0 = pm.n0;
+    const int m = its ? its[q.b] : kmax;
+    SO* o = out + (long long)q.b * obs + q.row * n0;
+    for (int c = q.c0; c < n0; c += pm.n0p) {
         A acc = accumulate ? A(o[c]) : A(0);
         for (int k = 0; k < m; ++k) {
             Vec<SZ> Zk = Z0;
             Zk.d += k * zstride;
             if constexpr (PT<SZ>::scaled) Zk.sc += (k * zstride) / n0;
-            View<SZ> z = view_of(Zk, b, 0, n0);
-            acc += yk[k] * z.at(row, c);
+            View<SZ> z = view_of(Zk, q.b, 0, n0);
+            acc += (A)y[(long long)q.b * kmax + k] * z.at(q.row, c);
         }
         o[c] = (SO)acc;
     }
@@ -251,26 +268,24 @@ __global__ void __launch_bounds__(kBlock) k_combine(int n0, long long rows, int 
 // One warp per (item, spatial row); every stage of the row at once.
 // ---------------------------------------------------------------------------
 template <class SZ, class A>
-__global__ void __launch_bounds__(kBlock) k_theta(Geo g, int B, const int* active, Vec<SZ> Z, A* wv,
-                                                  long long wbs, int s, const double* coef, A tau,
-                                                  Faces<A> faces) {
-    long long w = gwarp();
-    if (w >= (long long)B * g.R) return;
-    int b = (int)(w / g.R);
-    long long row = w % g.R;
-    if (active && !active[b]) return;
-    int j = (int)(row % g.n1), k = (int)(row / g.n1);
-    A cf[kMaxS * kMaxS];
-    for (int i = 0; i < s * s; ++i) cf[i] = tau * (A)coef[i];
-    View<SZ> zs[kMaxS];
-    for (int i = 0; i < s; ++i) zs[i] = view_of(Z, b, (long long)i * g.nx, g.n0);
-    A* out = wv + (long long)b * wbs + row * g.n0;
-    for (int c = lane_id(); c < g.n0; c += kWarp) {
+__global__ void __launch_bounds__(kPtMaxThreads) k_theta(Geo g, PtMap pm, int B, const int* active, Vec<SZ> Z, A* wv,
+                                                long long wbs, int s, const double* coef, A tau, Faces<A> faces) {
+    pdl_prologue();
+    PtPos q = pt_pos(pm, B, g.R, active);
+    if (!q.valid) return;
+    const long long row = q.row;
+    const int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    A* out = wv + (long long)q.b * wbs + row * g.n0;
+    for (int c = q.c0; c < g.n0; c += pm.n0p) {
         A kz[kMaxS];
-        for (int i = 0; i < s; ++i) kz[i] = (A)fd_K(zs[i], g, faces, row, j, k, c);
         for (int i = 0; i < s; ++i) {
-            A acc = (A)zs[i].at(row, c);
-            for (int jj = 0; jj < s; ++jj) acc += cf[i * s + jj] * kz[jj];
+            View<SZ> zi = view_of(Z, q.b, (long long)i * g.nx, g.n0);
+            kz[i] = (A)fd_K(zi, g, faces, row, j, k, c);
+        }
+        for (int i = 0; i < s; ++i) {
+            View<SZ> zi = view_of(Z, q.b, (long long)i * g.nx, g.n0);
+            A acc = (A)zi.at(row, c);
+            for (int jj = 0; jj < s; ++jj) acc += tau * (A)coef[i * s + jj] * kz[jj];
             out[(long long)i * g.nx + c] = acc;
         }
     }
@@ -278,32 +293,29 @@ __global__ void __launch_bounds__(kBlock) k_theta(Geo g, int B, const int* activ
 
 // Rana stage-sweep right-hand side: out = V_stage - tau sum_j coef[j] K Z_j.
 template <class SV, class SZ>
-__global__ void __launch_bounds__(kBlock) k_rana_rhs(Geo g, int B, const int* active, Vec<SV> V, int stage,
-                                                     Vec<SZ> Z, int s, const double* coef,
-                                                     typename PT<SZ>::A tau, Faces<typename PT<SZ>::A> faces,
-                                                     Vec<SZ> out) {
+__global__ void __launch_bounds__(kPtMaxThreads) k_rana_rhs(Geo g, PtMap pm, int B, const int* active, Vec<SV> V, int stage,
+                                                   Vec<SZ> Z, int s, const double* coef, typename PT<SZ>::A tau,
+                                                   Faces<typename PT<SZ>::A> faces, Vec<SZ> out) {
+    pdl_prologue();
     using A = typename PT<SZ>::A;
-    long long w = gwarp();
-    if (w >= (long long)B * g.R) return;
-    int b = (int)(w / g.R);
-    long long row = w % g.R;
-    if (active && !active[b]) return;
-    int j = (int)(row % g.n1), k = (int)(row / g.n1);
-    View<SV> v = view_of(V, b, (long long)stage * g.nx, g.n0);
-    A cf[kMaxS];
-    View<SZ> zs[kMaxS];
-    int nz = 0;
-    for (int jj = 0; jj < s; ++jj)
-        if (coef[jj] != 0.0) {
-            cf[nz] = tau * (A)coef[jj];
-            zs[nz] = view_of(Z, b, (long long)jj * g.nx, g.n0);
-            ++nz;
-        }
+    PtPos q = pt_pos(pm, B, g.R, active);
+    if constexpr (!PT<SZ>::scaled) {
+        if (!q.valid) return;
+    }
+    const long long row = q.row;
+    const int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    View<SV> v = view_of(V, q.b, (long long)stage * g.nx, g.n0);
     SZ* o; float* osc;
-    row_store_ptrs(out, b, 0, row, g.n0, o, osc);
-    row_store<SZ>(o, osc, g.n0, lane_id(), [&](int c) -> A {
+    row_store_ptrs(out, q.b, 0, row, g.n0, o, osc);
+    pt_store<SZ>(o, osc, pm, q.c0, q.valid, [&](int c) -> A {
         A acc = (A)v.at(row, c);
-        for (int q = 0; q < nz; ++q) acc -= cf[q] * (A)fd_K(zs[q], g, faces, row, j, k, c);
+        for (int jj = 0; jj < s; ++jj) {
+            const double cf = coef[jj];
+            if (cf != 0.0) {
+                View<SZ> zj = view_of(Z, q.b, (long long)jj * g.nx, g.n0);
+                acc -= tau * (A)cf * (A)fd_K(zj, g, faces, row, j, k, c);
+            }
+        }
         return acc;
     });
 }
@@ -316,6 +328,7 @@ __global__ void __launch_bounds__(kBlock) k_rana_rhs(Geo g, int B, const int* ac
 template <class A>
 __global__ void k_schur_g(long long nx, int nt, int s, const double* r, const double* zV, const double* bw,
                           double tau, A* wbuf, double* zv0) {
+    pdl_prologue();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long tot = (long long)(nt + 1) * nx;
     if (i >= tot) return;
@@ -343,16 +356,19 @@ struct StepPtrs {
 };
 
 static __global__ void k_step_set(StepPtrs* sp, double* z, const double* r, int n) {
+    pdl_prologue();
     sp->z = z;
     sp->r = r;
     sp->n = n;
 }
 
-static __global__ void k_step_add(StepPtrs* sp, int d) { sp->n += d; }
+static __global__ void k_step_add(StepPtrs* sp, int d) {
+    pdl_prologue(); sp->n += d; }
 
 // t_i = K z_{v,n} for every stage i (the e (x) K z_{v,n} right-hand side).
 template <class A>
 __global__ void __launch_bounds__(kBlock) k_schur_rhs(Geo g, int s, const StepPtrs* sp, A* t, Faces<A> faces) {
+    pdl_prologue();
     long long row = gwarp();
     if (row >= g.R) return;
     int j = (int)(row % g.n1), k = (int)(row / g.n1);
@@ -369,6 +385,7 @@ __global__ void __launch_bounds__(kBlock) k_schur_update(Geo g, int s, const A* 
                                                          Vec<SZ> Z0, long long zstride, const double* y,
                                                          int kmax, const int* its, const double* bw,
                                                          double tau) {
+    pdl_prologue();
     long long row = gwarp();
     if (row >= g.R) return;
     const int n = sp->n;
@@ -398,6 +415,7 @@ __global__ void __launch_bounds__(kBlock) k_schur_update(Geo g, int s, const A* 
 // Transposed substitution: t_i = b_i u_{n+1}.
 template <class A>
 __global__ void k_schurT_rhs(long long nx, int s, const StepPtrs* sp, const double* bw, A* t) {
+    pdl_prologue();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)s * nx) return;
     int q = (int)(i / nx);
@@ -408,6 +426,7 @@ __global__ void k_schurT_rhs(long long nx, int s, const StepPtrs* sp, const doub
 template <class A>
 __global__ void __launch_bounds__(kBlock) k_schurT_update(Geo g, int s, const StepPtrs* sp, const A* q,
                                                           double tau, Faces<A> faces) {
+    pdl_prologue();
     long long row = gwarp();
     if (row >= g.R) return;
     int j = (int)(row % g.n1), k = (int)(row / g.n1);
@@ -429,6 +448,7 @@ __global__ void __launch_bounds__(kBlock) k_schurT_update(Geo g, int s, const St
 template <class A>
 __global__ void k_schurT_vrhs(long long nx, int nt, int s, const double* rV, const double* zv, const double* bw,
                               double tau, A* t) {
+    pdl_prologue();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long tot = (long long)nt * s * nx;
     if (i >= tot) return;
@@ -440,6 +460,7 @@ __global__ void k_schurT_vrhs(long long nx, int nt, int s, const double* rV, con
 
 template <class SI, class SO>
 __global__ void k_convert(const SI* in, SO* out, long long n) {
+    pdl_prologue();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (SO)in[i];
 }
@@ -462,6 +483,7 @@ struct Tab {
 
 static __global__ void __launch_bounds__(kBlock) k_matvec(Geo g, int nt, Tab tab, double tau, Faces<double> faces,
                                                    const double* x, double* y, const double* rhs, int transpose) {
+    pdl_prologue();
     long long w = gwarp();
     if (w >= (long long)(nt + 1) * g.R) return;
     int n = (int)(w / g.R);
@@ -516,6 +538,7 @@ static __global__ void __launch_bounds__(kBlock) k_matvec(Geo g, int nt, Tab tab
 
 // rhs = [u0 ; 0 ; f_{n,i}]  (FD, M = I)
 static __global__ void k_rhs(long long nx, int nt, int s, const double* f, int f_time_dep, const double* u0, double* out) {
+    pdl_prologue();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long nv = (long long)(nt + 1) * nx;
     long long tot = nv + (long long)nt * s * nx;
@@ -527,6 +550,7 @@ static __global__ void k_rhs(long long nx, int nt, int s, const double* f, int f
 
 // grad_f = sum_{n,i} lambda_{V,n,i}  (FD, M = I)
 static __global__ void k_grad_f(long long nx, int nt, int s, const double* lam, double* gf) {
+    pdl_prologue();
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nx) return;
     const double* lV = lam + (long long)(nt + 1) * nx;

@@ -68,37 +68,182 @@ __device__ __forceinline__ void level_apply(const LevelOp<S>& op, const View<SU>
     diag = sten_coef(op, g.d == 3 ? 13 : 4, p);
 }
 
-// x_out = x_in + omega D^{-1} (b - A x_in); x_in.d == nullptr means x_in = 0.
+// (A u)_P and a_PP for a level whose values come from a getter u(row, col)
+// (used by the fused kernels, where u is itself computed on the fly).
+template <class S, class G>
+__device__ __forceinline__ void level_apply_g(const LevelOp<S>& op, G&& u, long long row, int j, int k, int c,
+                                              typename PT<S>::A& Au, typename PT<S>::A& diag) {
+    using A = typename PT<S>::A;
+    const Geo& g = op.g;
+    if (op.fine) {
+        A uP = u(row, c);
+        A uW = c > 0 ? u(row, c - 1) : A(0);
+        A uE = c + 1 < g.n0 ? u(row, c + 1) : A(0);
+        A uS = j > 0 ? u(row - 1, c) : A(0);
+        A uN = j + 1 < g.n1 ? u(row + 1, c) : A(0);
+        A uD = A(0), uU = A(0);
+        if (g.d == 3) {
+            uD = k > 0 ? u(row - g.n1, c) : A(0);
+            uU = k + 1 < g.n2 ? u(row + g.n1, c) : A(0);
+        }
+        A Ku;
+        const Faces<A>& f = op.faces;
+        if (f.fx == nullptr) {
+            Ku = A(g.hx2) * (A(2) * uP - uW - uE) + A(g.hy2) * (A(2) * uP - uS - uN);
+            if (g.d == 3) Ku += A(g.hz2) * (A(2) * uP - uD - uU);
+        } else {
+            const long long fxi = row * (g.n0 + 1) + c;
+            const long long fyi = ((long long)k * (g.n1 + 1) + j) * g.n0 + c;
+            Ku = A(f.fx[fxi]) * (uP - uW) + A(f.fx[fxi + 1]) * (uP - uE) + A(f.fy[fyi]) * (uP - uS) +
+                 A(f.fy[fyi + g.n0]) * (uP - uN);
+            if (g.d == 3) {
+                const long long fzi = ((long long)k * g.n1 + j) * g.n0 + c;
+                Ku += A(f.fz[fzi]) * (uP - uD) + A(f.fz[fzi + (long long)g.n1 * g.n0]) * (uP - uU);
+            }
+        }
+        Au = op.sigma * uP + op.c * Ku;
+        diag = op.sigma + op.c * fd_K_diag<A>(g, op.faces, row, j, k, c);
+        return;
+    }
+    const long long p = row * g.n0 + c;
+    A acc = A(0);
+    const int zlo = g.d == 3 ? -1 : 0, zhi = g.d == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+        int kk = k + dz;
+        if (kk < 0 || kk >= g.n2) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int jj = j + dy;
+            if (jj < 0 || jj >= g.n1) continue;
+            long long rr = row + dy + (long long)dz * g.n1;
+            for (int dx = -1; dx <= 1; ++dx) {
+                int cc = c + dx;
+                if (cc < 0 || cc >= g.n0) continue;
+                int q = (dx + 1) + 3 * (dy + 1) + (g.d == 3 ? 9 * (dz + 1) : 0);
+                acc += sten_coef(op, q, p) * u(rr, cc);
+            }
+        }
+    }
+    Au = acc;
+    diag = sten_coef(op, g.d == 3 ? 13 : 4, p);
+}
+
 template <class S>
-__global__ void __launch_bounds__(kBlock) k_smooth(LevelOp<S> op, int B, const int* active, Vec<S> xin,
-                                                   Vec<S> bv, Vec<S> xout, typename PT<S>::A omega) {
+__device__ __forceinline__ typename PT<S>::A level_diag(const LevelOp<S>& op, long long row, int j, int k, int c) {
+    using A = typename PT<S>::A;
+    if (op.fine) return op.sigma + op.c * fd_K_diag<A>(op.g, op.faces, row, j, k, c);
+    return sten_coef(op, op.g.d == 3 ? 13 : 4, row * op.g.n0 + c);
+}
+
+// Two damped-Jacobi sweeps in one pass: the first sweep is recomputed at the
+// point and at its stencil neighbours (x_in.d == nullptr: zero initial guess).
+template <class S>
+__global__ void __launch_bounds__(kPtMaxThreads) k_smooth2(LevelOp<S> op, PtMap pm, int B, const int* active,
+                                                           Vec<S> xin, Vec<S> bv, Vec<S> xout,
+                                                           typename PT<S>::A omega) {
+    pdl_prologue();
     using A = typename PT<S>::A;
     const Geo g = op.g;
-    long long w = gwarp();
-    if (w >= (long long)B * g.R) return;
-    int b = (int)(w / g.R);
-    long long row = w % g.R;
-    if (active && !active[b]) return;
-    int j = (int)(row % g.n1), k = (int)(row / g.n1);
-    int lane = lane_id();
-    View<S> bb = view_of(bv, b, 0, g.n0);
+    PtPos q = pt_pos(pm, B, g.R, active);
+    if constexpr (!PT<S>::scaled) {
+        if (!q.valid) return;
+    }
+    const long long row = q.row;
+    const int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    View<S> bb = view_of(bv, q.b, 0, g.n0);
+    const bool has = xin.d != nullptr;
+    View<S> xx = has ? view_of(xin, q.b, 0, g.n0) : View<S>{nullptr, nullptr, g.n0};
+    auto x1 = [&](long long rr, int cc) -> A {
+        const int jj = (int)(rr % g.n1), kk = (int)(rr / g.n1);
+        if (!has) return omega * bb.at(rr, cc) / level_diag(op, rr, jj, kk, cc);
+        A Au, dg;
+        level_apply(op, xx, rr, jj, kk, cc, Au, dg);
+        return xx.at(rr, cc) + omega * (bb.at(rr, cc) - Au) / dg;
+    };
     S* out; float* osc;
-    row_store_ptrs(xout, b, 0, row, g.n0, out, osc);
-    if (xin.d == nullptr) {
-        row_store<S>(out, osc, g.n0, lane, [&](int c) -> A {
-            A Au, dg;
-            // diagonal only: A x = 0
-            if (op.fine) {
-                dg = op.sigma + op.c * fd_K_diag<A>(g, op.faces, row, j, k, c);
-            } else {
-                dg = sten_coef(op, g.d == 3 ? 13 : 4, row * g.n0 + c);
+    row_store_ptrs(xout, q.b, 0, row, g.n0, out, osc);
+    pt_store<S>(out, osc, pm, q.c0, q.valid, [&](int c) -> A {
+        A Au, dg;
+        level_apply_g(op, x1, row, j, k, c, Au, dg);
+        return x1(row, c) + omega * (bb.at(row, c) - Au) / dg;
+    });
+}
+
+// bc = P^T (b - A x) with the fine residual computed on the fly (coarse rows;
+// x.d == nullptr: x = 0, residual = b).
+template <class S>
+__global__ void __launch_bounds__(kPtMaxThreads) k_resid_restrict(LevelOp<S> op, Geo gc, PtMap pm, int B,
+                                                                  const int* active, Vec<S> xv, Vec<S> bv,
+                                                                  Vec<S> bcv) {
+    pdl_prologue();
+    using A = typename PT<S>::A;
+    const Geo gf = op.g;
+    PtPos q = pt_pos(pm, B, gc.R, active);
+    if constexpr (!PT<S>::scaled) {
+        if (!q.valid) return;
+    }
+    const long long row = q.row;
+    const int J = (int)(row % gc.n1), Kc = (int)(row / gc.n1);
+    View<S> bb = view_of(bv, q.b, 0, gf.n0);
+    const bool has = xv.d != nullptr;
+    View<S> xx = has ? view_of(xv, q.b, 0, gf.n0) : View<S>{nullptr, nullptr, gf.n0};
+    S* out; float* osc;
+    row_store_ptrs(bcv, q.b, 0, row, gc.n0, out, osc);
+    pt_store<S>(out, osc, pm, q.c0, q.valid, [&](int I) -> A {
+        A acc = A(0);
+        const int zlo = gf.d == 3 ? -1 : 0, zhi = gf.d == 3 ? 1 : 0;
+        for (int dz = zlo; dz <= zhi; ++dz) {
+            int fk = gf.d == 3 ? 2 * Kc + 1 + dz : 0;
+            if (fk < 0 || fk >= gf.n2) continue;
+            A wz = dz == 0 ? A(1) : A(0.5);
+            for (int dy = -1; dy <= 1; ++dy) {
+                int fj = 2 * J + 1 + dy;
+                if (fj < 0 || fj >= gf.n1) continue;
+                A wy = dy == 0 ? A(1) : A(0.5);
+                long long frow = fj + (long long)gf.n1 * fk;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int fi = 2 * I + 1 + dx;
+                    if (fi < 0 || fi >= gf.n0) continue;
+                    A wx = dx == 0 ? A(1) : A(0.5);
+                    A r = bb.at(frow, fi);
+                    if (has) {
+                        A Au, dg;
+                        level_apply(op, xx, frow, fj, fk, fi, Au, dg);
+                        r -= Au;
+                    }
+                    acc += wx * wy * wz * r;
+                }
             }
-            (void)Au;
+        }
+        return acc;
+    });
+}
+
+// x_out = x_in + omega D^{-1} (b - A x_in); x_in.d == nullptr means x_in = 0.
+template <class S>
+__global__ void __launch_bounds__(kPtMaxThreads) k_smooth(LevelOp<S> op, PtMap pm, int B, const int* active, Vec<S> xin,
+                                                 Vec<S> bv, Vec<S> xout, typename PT<S>::A omega) {
+    pdl_prologue();
+    using A = typename PT<S>::A;
+    const Geo g = op.g;
+    PtPos q = pt_pos(pm, B, g.R, active);
+    if constexpr (!PT<S>::scaled) {
+        if (!q.valid) return;
+    }
+    const long long row = q.row;
+    const int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    View<S> bb = view_of(bv, q.b, 0, g.n0);
+    S* out; float* osc;
+    row_store_ptrs(xout, q.b, 0, row, g.n0, out, osc);
+    if (xin.d == nullptr) {
+        pt_store<S>(out, osc, pm, q.c0, q.valid, [&](int c) -> A {
+            A dg;
+            if (op.fine) dg = op.sigma + op.c * fd_K_diag<A>(g, op.faces, row, j, k, c);
+            else dg = sten_coef(op, g.d == 3 ? 13 : 4, row * g.n0 + c);
             return omega * bb.at(row, c) / dg;
         });
     } else {
-        View<S> xx = view_of(xin, b, 0, g.n0);
-        row_store<S>(out, osc, g.n0, lane, [&](int c) -> A {
+        View<S> xx = view_of(xin, q.b, 0, g.n0);
+        pt_store<S>(out, osc, pm, q.c0, q.valid, [&](int c) -> A {
             A Au, dg;
             level_apply(op, xx, row, j, k, c, Au, dg);
             return xx.at(row, c) + omega * (bb.at(row, c) - Au) / dg;
@@ -108,42 +253,44 @@ __global__ void __launch_bounds__(kBlock) k_smooth(LevelOp<S> op, int B, const i
 
 // r = b - A x
 template <class S>
-__global__ void __launch_bounds__(kBlock) k_residual(LevelOp<S> op, int B, const int* active, Vec<S> xv,
-                                                     Vec<S> bv, Vec<S> rv) {
+__global__ void __launch_bounds__(kPtMaxThreads) k_residual(LevelOp<S> op, PtMap pm, int B, const int* active, Vec<S> xv,
+                                                   Vec<S> bv, Vec<S> rv) {
+    pdl_prologue();
     using A = typename PT<S>::A;
     const Geo g = op.g;
-    long long w = gwarp();
-    if (w >= (long long)B * g.R) return;
-    int b = (int)(w / g.R);
-    long long row = w % g.R;
-    if (active && !active[b]) return;
-    int j = (int)(row % g.n1), k = (int)(row / g.n1);
-    View<S> xx = view_of(xv, b, 0, g.n0);
-    View<S> bb = view_of(bv, b, 0, g.n0);
+    PtPos q = pt_pos(pm, B, g.R, active);
+    if constexpr (!PT<S>::scaled) {
+        if (!q.valid) return;
+    }
+    const long long row = q.row;
+    const int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    View<S> xx = view_of(xv, q.b, 0, g.n0);
+    View<S> bb = view_of(bv, q.b, 0, g.n0);
     S* out; float* osc;
-    row_store_ptrs(rv, b, 0, row, g.n0, out, osc);
-    row_store<S>(out, osc, g.n0, lane_id(), [&](int c) -> A {
+    row_store_ptrs(rv, q.b, 0, row, g.n0, out, osc);
+    pt_store<S>(out, osc, pm, q.c0, q.valid, [&](int c) -> A {
         A Au, dg;
         level_apply(op, xx, row, j, k, c, Au, dg);
         return bb.at(row, c) - Au;
     });
 }
 
-// bc = P^T r  (coarse row kernel)
+// bc = P^T r  (coarse row kernel; pm maps the coarse rows)
 template <class S>
-__global__ void __launch_bounds__(kBlock) k_restrict(Geo gf, Geo gc, int B, const int* active, Vec<S> rv,
-                                                     Vec<S> bcv) {
+__global__ void __launch_bounds__(kPtMaxThreads) k_restrict(Geo gf, Geo gc, PtMap pm, int B, const int* active, Vec<S> rv,
+                                                   Vec<S> bcv) {
+    pdl_prologue();
     using A = typename PT<S>::A;
-    long long w = gwarp();
-    if (w >= (long long)B * gc.R) return;
-    int b = (int)(w / gc.R);
-    long long row = w % gc.R;
-    if (active && !active[b]) return;
-    int J = (int)(row % gc.n1), Kc = (int)(row / gc.n1);
-    View<S> rr = view_of(rv, b, 0, gf.n0);
+    PtPos q = pt_pos(pm, B, gc.R, active);
+    if constexpr (!PT<S>::scaled) {
+        if (!q.valid) return;
+    }
+    const long long row = q.row;
+    const int J = (int)(row % gc.n1), Kc = (int)(row / gc.n1);
+    View<S> rr = view_of(rv, q.b, 0, gf.n0);
     S* out; float* osc;
-    row_store_ptrs(bcv, b, 0, row, gc.n0, out, osc);
-    row_store<S>(out, osc, gc.n0, lane_id(), [&](int I) -> A {
+    row_store_ptrs(bcv, q.b, 0, row, gc.n0, out, osc);
+    pt_store<S>(out, osc, pm, q.c0, q.valid, [&](int I) -> A {
         A acc = A(0);
         const int zlo = gf.d == 3 ? -1 : 0, zhi = gf.d == 3 ? 1 : 0;
         for (int dz = zlo; dz <= zhi; ++dz) {
@@ -185,25 +332,26 @@ __device__ __forceinline__ int interp_1d(int F, int nc, int* J, float* wt) {
 
 // x_out = x_in + P xc  (fine row kernel); x_in.d == nullptr means 0.
 template <class S>
-__global__ void __launch_bounds__(kBlock) k_prolong_add(Geo gf, Geo gc, int B, const int* active, Vec<S> xcv,
-                                                        Vec<S> xin, Vec<S> xout) {
+__global__ void __launch_bounds__(kPtMaxThreads) k_prolong_add(Geo gf, Geo gc, PtMap pm, int B, const int* active,
+                                                      Vec<S> xcv, Vec<S> xin, Vec<S> xout) {
+    pdl_prologue();
     using A = typename PT<S>::A;
-    long long w = gwarp();
-    if (w >= (long long)B * gf.R) return;
-    int b = (int)(w / gf.R);
-    long long row = w % gf.R;
-    if (active && !active[b]) return;
-    int j = (int)(row % gf.n1), k = (int)(row / gf.n1);
-    View<S> xc = view_of(xcv, b, 0, gc.n0);
+    PtPos q = pt_pos(pm, B, gf.R, active);
+    if constexpr (!PT<S>::scaled) {
+        if (!q.valid) return;
+    }
+    const long long row = q.row;
+    const int j = (int)(row % gf.n1), k = (int)(row / gf.n1);
+    View<S> xc = view_of(xcv, q.b, 0, gc.n0);
     const bool has_in = xin.d != nullptr;
-    View<S> xi = has_in ? view_of(xin, b, 0, gf.n0) : View<S>{nullptr, nullptr, gf.n0};
+    View<S> xi = has_in ? view_of(xin, q.b, 0, gf.n0) : View<S>{nullptr, nullptr, gf.n0};
     int Jy[2], Jz[2] = {0, 0};
     float wy[2], wz[2] = {1.f, 0.f};
     int my = interp_1d(j, gc.n1, Jy, wy);
     int mz = gf.d == 3 ? interp_1d(k, gc.n2, Jz, wz) : 1;
     S* out; float* osc;
-    row_store_ptrs(xout, b, 0, row, gf.n0, out, osc);
-    row_store<S>(out, osc, gf.n0, lane_id(), [&](int c) -> A {
+    row_store_ptrs(xout, q.b, 0, row, gf.n0, out, osc);
+    pt_store<S>(out, osc, pm, q.c0, q.valid, [&](int c) -> A {
         int Jx[2];
         float wx[2];
         int mx = interp_1d(c, gc.n0, Jx, wx);
@@ -218,25 +366,69 @@ __global__ void __launch_bounds__(kBlock) k_prolong_add(Geo gf, Geo gc, int B, c
     });
 }
 
+// x_out = xp + omega D^{-1} (b - A xp) with xp = x_in + P xc computed on the fly at
+// the point and its stencil neighbours (prolongation fused with one sweep).
+template <class S>
+__global__ void __launch_bounds__(kPtMaxThreads) k_prolong_smooth(LevelOp<S> op, Geo gc, PtMap pm, int B,
+                                                                  const int* active, Vec<S> xcv, Vec<S> xin,
+                                                                  Vec<S> bv, Vec<S> xout, typename PT<S>::A omega) {
+    pdl_prologue();
+    using A = typename PT<S>::A;
+    const Geo gf = op.g;
+    PtPos q = pt_pos(pm, B, gf.R, active);
+    if constexpr (!PT<S>::scaled) {
+        if (!q.valid) return;
+    }
+    const long long row = q.row;
+    const int j = (int)(row % gf.n1), k = (int)(row / gf.n1);
+    View<S> xc = view_of(xcv, q.b, 0, gc.n0);
+    View<S> bb = view_of(bv, q.b, 0, gf.n0);
+    const bool has = xin.d != nullptr;
+    View<S> xi = has ? view_of(xin, q.b, 0, gf.n0) : View<S>{nullptr, nullptr, gf.n0};
+    auto xp = [&](long long rr, int cc) -> A {
+        const int jj = (int)(rr % gf.n1), kk = (int)(rr / gf.n1);
+        int Jx[2], Jy[2], Jz[2] = {0, 0};
+        float wx[2], wy[2], wz[2] = {1.f, 0.f};
+        int mx = interp_1d(cc, gc.n0, Jx, wx);
+        int my = interp_1d(jj, gc.n1, Jy, wy);
+        int mz = gf.d == 3 ? interp_1d(kk, gc.n2, Jz, wz) : 1;
+        A acc = has ? xi.at(rr, cc) : A(0);
+        for (int a = 0; a < mz; ++a)
+            for (int bq = 0; bq < my; ++bq) {
+                long long crow = Jy[bq] + (long long)gc.n1 * Jz[a];
+                A wyz = A(wy[bq]) * A(wz[a]);
+                for (int e = 0; e < mx; ++e) acc += wyz * A(wx[e]) * xc.at(crow, Jx[e]);
+            }
+        return acc;
+    };
+    S* out; float* osc;
+    row_store_ptrs(xout, q.b, 0, row, gf.n0, out, osc);
+    pt_store<S>(out, osc, pm, q.c0, q.valid, [&](int c) -> A {
+        A Au, dg;
+        level_apply_g(op, xp, row, j, k, c, Au, dg);
+        return xp(row, c) + omega * (bb.at(row, c) - Au) / dg;
+    });
+}
+
 // x = Dinv b at the coarsest level (Dinv dense, nc x nc, row-major, arithmetic type).
 template <class S>
-__global__ void __launch_bounds__(kBlock) k_coarse_solve(Geo g, int B, const int* active,
-                                                         const typename PT<S>::A* Dinv, Vec<S> bv,
-                                                         Vec<S> xv) {
+__global__ void __launch_bounds__(kPtMaxThreads) k_coarse_solve(Geo g, PtMap pm, int B, const int* active,
+                                                       const typename PT<S>::A* Dinv, Vec<S> bv, Vec<S> xv) {
+    pdl_prologue();
     using A = typename PT<S>::A;
-    long long w = gwarp();
-    if (w >= (long long)B * g.R) return;
-    int b = (int)(w / g.R);
-    long long row = w % g.R;
-    if (active && !active[b]) return;
-    View<S> bb = view_of(bv, b, 0, g.n0);
+    PtPos q = pt_pos(pm, B, g.R, active);
+    if constexpr (!PT<S>::scaled) {
+        if (!q.valid) return;
+    }
+    const long long row = q.row;
+    View<S> bb = view_of(bv, q.b, 0, g.n0);
     S* out; float* osc;
-    row_store_ptrs(xv, b, 0, row, g.n0, out, osc);
+    row_store_ptrs(xv, q.b, 0, row, g.n0, out, osc);
     const int nc = (int)g.nx;
-    row_store<S>(out, osc, g.n0, lane_id(), [&](int c) -> A {
+    pt_store<S>(out, osc, pm, q.c0, q.valid, [&](int c) -> A {
         long long p = row * g.n0 + c;
         A acc = A(0);
-        for (int q = 0; q < nc; ++q) acc += Dinv[p * nc + q] * bb.at(q / g.n0, q % g.n0);
+        for (int qq = 0; qq < nc; ++qq) acc += Dinv[p * nc + qq] * bb.at(qq / g.n0, qq % g.n0);
         return acc;
     });
 }
@@ -308,6 +500,7 @@ __device__ __forceinline__ int fine_row_entries(const FineDesc& fd, int fi, int 
 }
 
 static __global__ void k_galerkin(FineDesc fd, Geo gc, double* out) {
+    pdl_prologue();
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= gc.nx) return;
     const Geo& gf = fd.g;
@@ -353,6 +546,7 @@ static __global__ void k_galerkin(FineDesc fd, Geo gc, double* out) {
 
 // Dense matrix of the coarsest level from its FP64 description (fine or stencil).
 static __global__ void k_dense_level(FineDesc fd, double* Adense) {
+    pdl_prologue();
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const Geo& g = fd.g;
     if (p >= g.nx) return;
@@ -369,6 +563,7 @@ static __global__ void k_dense_level(FineDesc fd, double* Adense) {
 
 // In-place Gauss--Jordan inverse (SPD input, no pivoting needed), one block.
 static __global__ void k_gauss_jordan(double* A, double* Inv, int n, int* fail) {
+    pdl_prologue();
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Inv[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
     __syncthreads();
     for (int k = 0; k < n; ++k) {
@@ -400,6 +595,7 @@ static __global__ void k_gauss_jordan(double* A, double* Inv, int n, int* fail) 
 
 // Per-component max |coef| (one block per component) and conversion to S.
 static __global__ void k_stencil_absmax(const double* sten, long long nx, float* cmax) {
+    pdl_prologue();
     int q = blockIdx.x;
     double m = 0.0;
     for (long long p = threadIdx.x; p < nx; p += blockDim.x) m = fmax(m, fabs(sten[(long long)q * nx + p]));
@@ -424,6 +620,7 @@ static __global__ void k_stencil_absmax(const double* sten, long long nx, float*
 
 template <class S>
 __global__ void k_stencil_convert(const double* sten, long long nx, int ncoef, const float* sc, S* out) {
+    pdl_prologue();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nx * ncoef) return;
     int q = (int)(i / nx);
@@ -434,6 +631,7 @@ __global__ void k_stencil_convert(const double* sten, long long nx, int ncoef, c
 
 template <class A>
 __global__ void k_convert_dense(const double* in, A* out, long long n) {
+    pdl_prologue();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (A)in[i];
 }
@@ -450,24 +648,36 @@ namespace aao {
 // chip are not rounded to the 16-bit storage format (that format is for data
 // that travels through HBM).
 // ---------------------------------------------------------------------------
-constexpr int kTailPmax = 16;   // points per thread at level lc
-constexpr int kTailMaxPoints = 2048;
+constexpr int kTailPmax = 4;    // points per thread at level lc (kTailMaxPoints / 1024)
+constexpr int kTailMaxPoints = 4096;
+constexpr long long kFuseMaxPoints = 1 << 20;   // fuse sweeps below this many points per launch
 
 template <class SI> struct TailCtx {
     using A = typename PT<SI>::A;
     int lc, L;
     LevelOp<SI> op[kMaxLevels];
-    int off[kMaxLevels];        // smem offset (A elements) of X_l; B_l follows
+    int off[kMaxLevels];        // smem offset (A elements) of X_l; B_l and R_l follow
+    int vec_bytes;              // bytes of all X_l, B_l
+    int stage_from;             // levels >= stage_from (and >= 1) read their stencil from smem
+    int sten_off[kMaxLevels];   // byte offset of a staged stencil (after the vectors)
     const A* Dinv;
     A omega;
     int nu1, nu2;
 };
 
+// The operator of tail level l, reading a staged stencil from shared memory.
+template <class SI>
+__device__ __forceinline__ LevelOp<SI> tail_op(const TailCtx<SI>& t, int l, const unsigned char* smem) {
+    LevelOp<SI> op = t.op[l];
+    if (l >= 1 && l >= t.stage_from) op.sten = reinterpret_cast<const SI*>(smem + t.sten_off[l]);
+    return op;
+}
+
 template <class SI>
 __device__ __forceinline__ void tail_smooth(const TailCtx<SI>& t, int l, typename PT<SI>::A* sm, int sweeps,
                                             bool zero_first) {
     using A = typename PT<SI>::A;
-    const LevelOp<SI>& op = t.op[l];
+    const LevelOp<SI> op = tail_op(t, l, reinterpret_cast<const unsigned char*>(sm));
     const Geo& g = op.g;
     A* X = sm + t.off[l];
     const A* Bv = X + g.nx;
@@ -508,6 +718,7 @@ __device__ __forceinline__ void tail_smooth(const TailCtx<SI>& t, int l, typenam
 template <class SI>
 __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, const int* active, Vec<SI> bv,
                                                       Vec<SI> xin, Vec<SI> xout) {
+    pdl_prologue();
     using A = typename PT<SI>::A;
     extern __shared__ __align__(16) unsigned char tail_smem[];
     A* sm = reinterpret_cast<A*>(tail_smem);
@@ -515,6 +726,13 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
     if (b >= B || (active && !active[b])) return;
     const int nt = blockDim.x, tid = threadIdx.x;
     const int lc = t.lc, L = t.L;
+    // copy the coarse stencils of levels >= stage_from into shared memory
+    for (int l = t.stage_from; l < L; ++l) {
+        if (l < 1) continue;
+        const long long n = (long long)t.op[l].ncoef * t.op[l].g.nx;
+        SI* dst = reinterpret_cast<SI*>(tail_smem + t.sten_off[l]);
+        for (long long i = tid; i < n; i += nt) dst[i] = t.op[l].sten[i];
+    }
     {
         const Geo& g = t.op[lc].g;
         A* X = sm + t.off[lc];
@@ -531,7 +749,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
     __syncthreads();
     bool xzero = xin.d == nullptr;
     for (int l = lc; l < L - 1; ++l) {
-        const LevelOp<SI>& op = t.op[l];
+        const LevelOp<SI> op = tail_op(t, l, tail_smem);
         const Geo& gf = op.g;
         const Geo& gc = t.op[l + 1].g;
         A* X = sm + t.off[l];
@@ -542,7 +760,22 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
         }
         A* Xc = sm + t.off[l + 1];
         A* Bc = Xc + gc.nx;
-        View<A> xv{X, nullptr, gf.n0};
+        A* Rf = Bv + gf.nx;
+        // residual of this level once (on chip), then the restriction P^T r
+        if (xzero) {
+            for (int p = tid; p < gf.nx; p += nt) Rf[p] = Bv[p];
+        } else {
+            View<A> xv{X, nullptr, gf.n0};
+            for (int p = tid; p < gf.nx; p += nt) {
+                int c = p % gf.n0;
+                long long row = p / gf.n0;
+                int j = (int)(row % gf.n1), k = (int)(row / gf.n1);
+                A Au, dg;
+                level_apply(op, xv, row, j, k, c, Au, dg);
+                Rf[p] = Bv[p] - Au;
+            }
+        }
+        __syncthreads();
         for (int P = tid; P < gc.nx; P += nt) {
             int I = P % gc.n0;
             long long crow = P / gc.n0;
@@ -562,13 +795,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
                         int fi = 2 * I + 1 + dx;
                         if (fi < 0 || fi >= gf.n0) continue;
                         A wx = dx == 0 ? A(1) : A(0.5);
-                        A r = Bv[frow * gf.n0 + fi];
-                        if (!xzero) {
-                            A Au, dg;
-                            level_apply(op, xv, frow, fj, fk, fi, Au, dg);
-                            r -= Au;
-                        }
-                        acc += wx * wy * wz * r;
+                        acc += wx * wy * wz * Rf[frow * gf.n0 + fi];
                     }
                 }
             }

@@ -197,13 +197,15 @@ extern "C" aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double 
                               const double* dinv, int pre, int post, double omega, cudaStream_t st,
                               const LevelOp<double>* ops) {
             const Geo& gl = lev[l];
-            unsigned nb = blocks_for_rows(gl.R);
+            const PtMap pm = ptmap(gl.n0);
             if (l == L - 1) {
-                launch(k_coarse_solve<double>, nb, kBlock, 0, st, gl, 1, (const int*)nullptr, dinv, bvec, xout);
+                launch(k_coarse_solve<double>, pt_blocks(pm, gl.R), pt_threads(pm), 0, st, gl, pm, 1, (const int*)nullptr, dinv,
+                       bvec, xout);
                 AAO_LAUNCH_CHECK();
                 return AAO_OK;
             }
             const LevelOp<double>& op = ops[l];
+            const PtMap pmc = ptmap(lev[l + 1].n0);
             const int nops = pre + 1 + post;
             int opi = 0;
             Vec<double> cur = xin;
@@ -214,16 +216,18 @@ extern "C" aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double 
             };
             for (int q = 0; q < pre; ++q) {
                 Vec<double> d = dest();
-                launch(k_smooth<double>, nb, kBlock, 0, st, op, 1, (const int*)nullptr, cur, bvec, d, omega);
+                launch(k_smooth<double>, pt_blocks(pm, gl.R), pt_threads(pm), 0, st, op, pm, 1, (const int*)nullptr, cur,
+                       bvec, d, omega);
                 cur = d;
             }
             const Geo& gc = lev[l + 1];
             if (cur.d == nullptr) {
-                launch(k_restrict<double>, blocks_for_rows(gc.R), kBlock, 0, st, gl, gc, 1, (const int*)nullptr, bvec,
+                launch(k_restrict<double>, pt_blocks(pmc, gc.R), pt_threads(pmc), 0, st, gl, gc, pmc, 1, (const int*)nullptr, bvec,
                        Bb[l + 1]);
             } else {
-                launch(k_residual<double>, nb, kBlock, 0, st, op, 1, (const int*)nullptr, cur, bvec, Rr[l]);
-                launch(k_restrict<double>, blocks_for_rows(gc.R), kBlock, 0, st, gl, gc, 1, (const int*)nullptr,
+                launch(k_residual<double>, pt_blocks(pm, gl.R), pt_threads(pm), 0, st, op, pm, 1, (const int*)nullptr, cur, bvec,
+                       Rr[l]);
+                launch(k_restrict<double>, pt_blocks(pmc, gc.R), pt_threads(pmc), 0, st, gl, gc, pmc, 1, (const int*)nullptr,
                        Rr[l], Bb[l + 1]);
             }
             AAO_LAUNCH_CHECK();
@@ -231,12 +235,14 @@ extern "C" aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double 
                         st, ops));
             {
                 Vec<double> d = dest();
-                launch(k_prolong_add<double>, nb, kBlock, 0, st, gl, gc, 1, (const int*)nullptr, X[l + 1], cur, d);
+                launch(k_prolong_add<double>, pt_blocks(pm, gl.R), pt_threads(pm), 0, st, gl, gc, pm, 1, (const int*)nullptr,
+                       X[l + 1], cur, d);
                 cur = d;
             }
             for (int q = 0; q < post; ++q) {
                 Vec<double> d = dest();
-                launch(k_smooth<double>, nb, kBlock, 0, st, op, 1, (const int*)nullptr, cur, bvec, d, omega);
+                launch(k_smooth<double>, pt_blocks(pm, gl.R), pt_threads(pm), 0, st, op, pm, 1, (const int*)nullptr, cur,
+                       bvec, d, omega);
                 cur = d;
             }
             AAO_LAUNCH_CHECK();

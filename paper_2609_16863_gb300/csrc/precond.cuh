@@ -248,18 +248,29 @@ class Precond : public PrecondBase {
         // ---- fused tail: the coarsest levels that fit on one SM
         {
             const size_t cap = 200 * 1024;
+            const int ncf = g0.d == 3 ? 27 : 9;
             lc = L - 1;
             size_t acc = 0;
             for (int l = L - 1; l >= 0; --l) {
-                acc += 2 * (size_t)lev[l].g.nx * sizeof(A);
-                // the tail runs on one SM: keep its top level small enough that the
-                // Galerkin stencils it reads stay resident in L1
-                if (lev[l].g.nx > kTailMaxPoints || acc > cap) break;
+                acc += 3 * (size_t)lev[l].g.nx * sizeof(A);
+                // the tail runs on one SM: its top level stays small
+                if (lev[l].g.nx > kTailMaxPoints || lev[l].g.nx > (long long)kTailPmax * tail_threads || acc > cap)
+                    break;
                 lc = l;
             }
-            int off = 0;
-            for (int l = lc; l < L; ++l) off += 2 * (int)lev[l].g.nx;
-            tail_smem = (size_t)off * sizeof(A);
+            size_t vec_bytes = 0;
+            for (int l = lc; l < L; ++l) vec_bytes += 3 * (size_t)lev[l].g.nx * sizeof(A);
+            vec_bytes = (vec_bytes + 15) / 16 * 16;
+            // stage as many of the coarsest stencils as fit next to the vectors
+            int stage_from = L;
+            size_t sb = 0;
+            for (int l = L - 1; l >= (lc > 1 ? lc : 1); --l) {
+                size_t add = ((size_t)ncf * lev[l].g.nx * sizeof(SI) + 15) / 16 * 16;
+                if (vec_bytes + sb + add > cap) break;
+                sb += add;
+                stage_from = l;
+            }
+            tail_smem = vec_bytes + sb;
             for (int i = 0; i < s; ++i) {
                 TailCtx<SI>& t = tctx[i];
                 t.lc = lc;
@@ -268,15 +279,31 @@ class Precond : public PrecondBase {
                 for (int l = lc; l < L; ++l) {
                     t.op[l] = level_op(l, i);
                     t.off[l] = o;
-                    o += 2 * (int)lev[l].g.nx;
+                    o += 3 * (int)lev[l].g.nx;
+                }
+                t.vec_bytes = (int)vec_bytes;
+                t.stage_from = stage_from;
+                size_t so = vec_bytes;
+                for (int l = 0; l < kMaxLevels; ++l) t.sten_off[l] = 0;
+                for (int l = stage_from; l < L; ++l) {
+                    t.sten_off[l] = (int)so;
+                    so += ((size_t)ncf * lev[l].g.nx * sizeof(SI) + 15) / 16 * 16;
                 }
                 t.Dinv = Dinv[i];
                 t.omega = (A)h->opt.mg_omega;
                 t.nu1 = h->opt.mg_pre;
                 t.nu2 = h->opt.mg_post;
             }
-            AAO_CUDA_TRY(cudaFuncSetAttribute(k_vcycle_tail<SI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)tail_smem));
+            // the attribute is per kernel for the whole process: always set the device's
+            // opt-in maximum so that handles with larger tails keep working
+            int dev = 0, optin = 0;
+            AAO_CUDA_TRY(cudaGetDevice(&dev));
+            AAO_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            if ((int)tail_smem > optin) {
+                set_error("fused multigrid tail does not fit in shared memory");
+                return AAO_ERR_ARG;
+            }
+            AAO_CUDA_TRY(cudaFuncSetAttribute(k_vcycle_tail<SI>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         }
         // ---- level scratch
         for (int l = 0; l < L; ++l) {
@@ -354,7 +381,8 @@ class Precond : public PrecondBase {
     // x_out = V-cycle(l) applied to (x_in, b); x_in.d == nullptr: zero guess.
     aao_status vcycle(int l, int stage, int B, const int* act, Vec<SI> xin, Vec<SI> b, Vec<SI> xout) {
         const Geo& g = lev[l].g;
-        unsigned nb = blocks_for_rows((long long)B * g.R);
+        const PtMap pm = ptmap(g.n0);
+        const unsigned pbl = pt_blocks(pm, (long long)B * g.R), pth = pt_threads(pm);
         if (l == lc) {
             bytes_hint((xin.d ? 3.0 : 2.0) * nact * g.nx * sizeof(SI));
             launch(k_vcycle_tail<SI>, (unsigned)B, tail_threads, tail_smem, st(), tctx[stage], B, act, b, xin, xout);
@@ -363,14 +391,27 @@ class Precond : public PrecondBase {
         }
         if (l == L - 1) {
             bytes_hint(2.0 * nact * g.nx * sizeof(SI));
-            launch(k_coarse_solve<SI>, nb, kBlock, 0, st(), g, B, act, Dinv[stage], b, xout);
+            launch(k_coarse_solve<SI>, pt_blocks(pm, (long long)B * g.R), pt_threads(pm), 0, st(), g, pm, B, act, Dinv[stage], b,
+                   xout);
             AAO_LAUNCH_CHECK();
             return AAO_OK;
         }
         LevelOp<SI> op = level_op(l, stage);
+        const Geo& gc = lev[l + 1].g;
+        const PtMap pmc = ptmap(gc.n0);
+        const unsigned cbl = pt_blocks(pmc, (long long)B * gc.R), cth = pt_threads(pmc);
         const A om = (A)h->opt.mg_omega;
         const int nu1 = h->opt.mg_pre, nu2 = h->opt.mg_post;
-        const int nops = nu1 + 1 + nu2;
+        // Fused kernels trade recomputation for launches: they pay off where the
+        // V-cycle is latency bound (small batches: the Schur sweep), not in the
+        // bandwidth- or FP64-bound batched phase.  Only on 2D levels and on the
+        // matrix-free fine level (a 27-point stored stencil makes the neighbour
+        // recomputation too costly).
+        const bool fuse = (long long)B * g.nx <= kFuseMaxPoints && (g.d == 2 || op.fine);
+        const bool f2 = fuse && nu1 >= 2, fps = fuse && nu2 >= 1;
+        const int pre_l = f2 ? nu1 - 1 : nu1;
+        const int post_l = fps ? nu2 : nu2 + 1;
+        const int nops = pre_l + post_l;
         Vec<SI> cur = xin;
         int opi = 0;
         auto dest = [&](void) -> Vec<SI> {
@@ -378,40 +419,53 @@ class Precond : public PrecondBase {
             if (opi == nops) return xout;
             return (cur.d == lev[l].T0.d) ? lev[l].T1 : lev[l].T0;
         };
-        for (int q = 0; q < nu1; ++q) {
+        int q = 0;
+        if (f2) {
             Vec<SI> d = dest();
             bytes_hint((cur.d ? 3.0 : 2.0) * nact * g.nx * sizeof(SI));
-            launch(k_smooth<SI>, nb, kBlock, 0, st(), op, B, act, cur, b, d, om);
+            launch(k_smooth2<SI>, pbl, pth, 0, st(), op, pm, B, act, cur, b, d, om);
+            cur = d;
+            q = 2;
+        }
+        for (; q < nu1; ++q) {
+            Vec<SI> d = dest();
+            bytes_hint((cur.d ? 3.0 : 2.0) * nact * g.nx * sizeof(SI));
+            launch(k_smooth<SI>, pbl, pth, 0, st(), op, pm, B, act, cur, b, d, om);
             cur = d;
         }
         // residual and restriction
-        Vec<SI> zero{};
-        if (cur.d == nullptr) {
-            // no pre-smoothing from a zero guess: residual = b
-            const Geo& gc = lev[l + 1].g;
+        if (fuse) {
+            bytes_hint(((cur.d ? 2.0 : 1.0) * g.nx + gc.nx) * nact * sizeof(SI));
+            launch(k_resid_restrict<SI>, cbl, cth, 0, st(), op, gc, pmc, B, act, cur, b, lev[l + 1].Bb);
+        } else if (cur.d == nullptr) {
             bytes_hint(1.0 * nact * (g.nx + gc.nx) * sizeof(SI));
-            launch(k_restrict<SI>, blocks_for_rows((long long)B * gc.R), kBlock, 0, st(), g, gc, B, act, b,
-                                                                                    lev[l + 1].Bb);
+            launch(k_restrict<SI>, cbl, cth, 0, st(), g, gc, pmc, B, act, b, lev[l + 1].Bb);
         } else {
             bytes_hint(3.0 * nact * g.nx * sizeof(SI));
-            launch(k_residual<SI>, nb, kBlock, 0, st(), op, B, act, cur, b, lev[l].Rr);
-            const Geo& gc = lev[l + 1].g;
+            launch(k_residual<SI>, pbl, pth, 0, st(), op, pm, B, act, cur, b, lev[l].Rr);
             bytes_hint(1.0 * nact * (g.nx + gc.nx) * sizeof(SI));
-            launch(k_restrict<SI>, blocks_for_rows((long long)B * gc.R), kBlock, 0, st(), g, gc, B, act, lev[l].Rr,
-                                                                                    lev[l + 1].Bb);
+            launch(k_restrict<SI>, cbl, cth, 0, st(), g, gc, pmc, B, act, lev[l].Rr, lev[l + 1].Bb);
         }
         AAO_LAUNCH_CHECK();
+        Vec<SI> zero{};
         AAO_TRY(vcycle(l + 1, stage, B, act, zero, lev[l + 1].Bb, lev[l + 1].X));
-        {
+        q = 0;
+        if (fps) {
             Vec<SI> d = dest();
-            bytes_hint(1.0 * nact * (lev[l + 1].g.nx + (cur.d ? 2.0 : 1.0) * g.nx) * sizeof(SI));
-            launch(k_prolong_add<SI>, nb, kBlock, 0, st(), g, lev[l + 1].g, B, act, lev[l + 1].X, cur, d);
+            bytes_hint(1.0 * nact * (gc.nx + (cur.d ? 3.0 : 2.0) * g.nx) * sizeof(SI));
+            launch(k_prolong_smooth<SI>, pbl, pth, 0, st(), op, gc, pm, B, act, lev[l + 1].X, cur, b, d, om);
+            cur = d;
+            q = 1;
+        } else {
+            Vec<SI> d = dest();
+            bytes_hint(1.0 * nact * (gc.nx + (cur.d ? 2.0 : 1.0) * g.nx) * sizeof(SI));
+            launch(k_prolong_add<SI>, pbl, pth, 0, st(), g, gc, pm, B, act, lev[l + 1].X, cur, d);
             cur = d;
         }
-        for (int q = 0; q < nu2; ++q) {
+        for (; q < nu2; ++q) {
             Vec<SI> d = dest();
             bytes_hint(3.0 * nact * g.nx * sizeof(SI));
-            launch(k_smooth<SI>, nb, kBlock, 0, st(), op, B, act, cur, b, d, om);
+            launch(k_smooth<SI>, pbl, pth, 0, st(), op, pm, B, act, cur, b, d, om);
             cur = d;
         }
         AAO_LAUNCH_CHECK();
@@ -428,12 +482,13 @@ class Precond : public PrecondBase {
     aao_status rana(int B, const int* act, Vec<SP> V, Vec<SI> Z, int transpose) {
         const Geo& g = h->g;
         const int s = h->s;
-        unsigned nb = blocks_for_rows((long long)B * g.R);
+        const PtMap pm0 = ptmap(g.n0);
         for (int t = 0; t < s; ++t) {
             int i = transpose ? s - 1 - t : t;
             const double* coef = (transpose ? h->d_LDb : h->d_LDf) + i * s;
             bytes_hint(1.0 * nact * g.nx * (sizeof(SP) + (transpose ? s - 1 - i : i) * sizeof(SI) + sizeof(SI)));
-            launch(k_rana_rhs<SP, SI>, nb, kBlock, 0, st(), g, B, act, V, i, Z, s, coef, (A)h->tau, facesA, mgb);
+            launch(k_rana_rhs<SP, SI>, pt_blocks(pm0, (long long)B * g.R), pt_threads(pm0), 0, st(), g, pm0, B, act, V, i, Z, s,
+                   coef, (A)h->tau, facesA, mgb);
             AAO_LAUNCH_CHECK();
             Vec<SI> Zi = shift_vec(Z, (long long)i * g.nx, g.n0);
             AAO_TRY(mg_solve(i, B, act, mgb, Zi));
@@ -451,15 +506,15 @@ class Precond : public PrecondBase {
         const int s = h->s;
         const long long item = (long long)s * g.nx;
         const long long rows = (long long)s * g.R;
-        const unsigned nb = blocks_for_rows((long long)B * rows);
-        const unsigned nbs = blocks_for_rows((long long)B * g.R);
+        const PtMap pm0 = ptmap(g.n0);
+        const unsigned nbp = pt_blocks(pm0, (long long)B * rows), ntp = pt_threads(pm0);
         Red red = h->red;
-        red.nchunk = h->nchunk_for(B, rows);
+        red.nchunk = h->nchunk_for(B, rows * ((g.n0 + kWarp - 1) / kWarp));
         dim3 rgrid(red.nchunk, B);
         launch(k_norm<SR>, rgrid, kBlock, 0, st(), g.n0, rows, B, nullptr, src, sbs, red, betah, 1);
         launch(k_inner_init, (B + 127) / 128, 128, 0, st(), B, kin, betah, activeh, itsh, gh, nonfin);
         refresh_nact(B);
-        launch(k_scale_store<SP, SR>, nb, kBlock, 0, st(), g.n0, rows, B, activeh, src, sbs, betah, 1, V0);
+        launch(k_scale_store<SP, SR>, nbp, ntp, 0, st(), pm0, (int)rows, B, activeh, src, sbs, (const double*)betah, 1LL, V0);
         AAO_LAUNCH_CHECK();
         const long long HS = (long long)(kin + 1) * kin;
         for (int k = 0; k < kin; ++k) {
@@ -467,7 +522,8 @@ class Precond : public PrecondBase {
             Vec<SI> Zk = shift_vec(Z0, k * zstride, g.n0);
             AAO_TRY(rana(B, activeh, Vk, Zk, transpose));
             bytes_hint(1.0 * nact * item * (sizeof(SI) + sizeof(A)));
-            launch(k_theta<SI, A>, nbs, kBlock, 0, st(), g, B, activeh, Zk, wv, item, s, transpose ? h->d_AT : h->d_A,
+            launch(k_theta<SI, A>, pt_blocks(pm0, (long long)B * g.R), pt_threads(pm0), 0, st(), g, pm0, B, (const int*)activeh, Zk,
+                   wv, item, s, transpose ? h->d_AT : h->d_A,
                                                      (A)h->tau, facesA);
             AAO_LAUNCH_CHECK();
             // modified Gram--Schmidt: h_{0,k} = V_0.w; then w -= h_{i-1,k} V_{i-1}, h_{i,k} = V_i.w
@@ -488,7 +544,7 @@ class Precond : public PrecondBase {
             refresh_nact(B);
             if (k + 1 < kin) {
                 Vec<SP> Vn = shift_vec(V0, (k + 1) * vstride, g.n0);
-                launch(k_scale_store<SP, A>, nb, kBlock, 0, st(), g.n0, rows, B, activeh, wv, item,
+                launch(k_scale_store<SP, A>, nbp, ntp, 0, st(), pm0, (int)rows, B, (const int*)activeh, (const A*)wv, item,
                                                               Hh + (k + 1) * kin + k, HS, Vn);
                 AAO_LAUNCH_CHECK();
             }
@@ -497,7 +553,8 @@ class Precond : public PrecondBase {
         launch(k_count_its, 1, 128, 0, st(), B, itsh, itcount);
         if (out) {
             Vec<SI> Zc = Z0;
-            launch(k_combine<SI, double>, nb, kBlock, 0, st(), g.n0, rows, B, Zc, zstride, yh, kin, itsh, out, obs, 0);
+            launch(k_combine<SI, double>, nbp, ntp, 0, st(), pm0, (int)rows, B, Zc, zstride, (const double*)yh, kin,
+                   (const int*)itsh, out, obs, 0);
         }
         AAO_LAUNCH_CHECK();
         return AAO_OK;
@@ -522,7 +579,8 @@ class Precond : public PrecondBase {
                    (const double*)h->d_b, tbuf);
             AAO_TRY(inner<A>(1, tbuf, item, nullptr, 0, 1));
             Vec<SI> Zc = Z0;
-            launch(k_combine<SI, A>, blocks_for_rows((long long)s * g.R), kBlock, 0, st(), g.n0, (long long)s * g.R, 1,
+            launch(k_combine<SI, A>, pt_blocks(ptmap(g.n0), (long long)s * g.R), pt_threads(ptmap(g.n0)), 0, st(), ptmap(g.n0),
+                   s * g.R, 1,
                    Zc, zstride, (const double*)yh, kin, (const int*)itsh, qbuf, item, 0);
             launch(k_schurT_update<A>, nbr, kBlock, 0, st(), g, s, (const StepPtrs*)stepp, (const A*)qbuf, h->tau,
                    facesA);
@@ -539,13 +597,15 @@ class Precond : public PrecondBase {
         if (!cap_stream) AAO_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
         cudaStream_t keep = cur_stream;
         cur_stream = cap_stream;
-        long long before = g_launches;
+        const long long before = g_thread_launches;
         AAO_CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
         aao_status st_ = schur_step(transpose);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
         cur_stream = keep;
-        g_launches = before;
+        // captured launches run only when the graph is replayed: count them there
+        g_launches -= g_thread_launches - before;
+        g_thread_launches = before;
         if (st_ != AAO_OK) return st_;
         if (e != cudaSuccess) {
             set_error(std::string("graph capture failed: ") + cudaGetErrorString(e));
@@ -626,12 +686,14 @@ class Precond : public PrecondBase {
     aao_status shifted_solve(int stage, const double* b, double* x) override {
         const Geo& g = h->g;
         nact = 1;
-        launch(k_scale_store<SI, double>, blocks_for_rows(g.R), kBlock, 0, st(), g.n0, g.R, 1, nullptr, b, g.nx,
+        launch(k_scale_store<SI, double>, pt_blocks(ptmap(g.n0), g.R), pt_threads(ptmap(g.n0)), 0, st(), ptmap(g.n0), g.R, 1,
+               (const int*)nullptr, b, g.nx,
                                                                              nullptr, 0, mgb);
         AAO_LAUNCH_CHECK();
         Vec<SI> out = Z0;   // item 0, stage 0 of the first Z basis
         AAO_TRY(mg_solve(stage, 1, nullptr, mgb, out));
-        launch(k_load<SI, double>, blocks_for_rows(g.R), kBlock, 0, st(), g.n0, g.R, 1, out, x, g.nx);
+        launch(k_load<SI, double>, pt_blocks(ptmap(g.n0), g.R), pt_threads(ptmap(g.n0)), 0, st(), ptmap(g.n0), g.R, 1, out, x,
+               g.nx);
         AAO_LAUNCH_CHECK();
         return AAO_OK;
     }
@@ -640,11 +702,13 @@ class Precond : public PrecondBase {
         const Geo& g = h->g;
         nact = 1;
         const long long rows = (long long)h->s * g.R;
-        launch(k_scale_store<SP, double>, blocks_for_rows(rows), kBlock, 0, st(), g.n0, rows, 1, nullptr, r,
+        launch(k_scale_store<SP, double>, pt_blocks(ptmap(g.n0), rows), pt_threads(ptmap(g.n0)), 0, st(), ptmap(g.n0),
+               (int)rows, 1, (const int*)nullptr, r,
                                                                               (long long)h->s * g.nx, nullptr, 0, V0);
         AAO_LAUNCH_CHECK();
         AAO_TRY(rana(1, nullptr, V0, Z0, transpose));
-        launch(k_load<SI, double>, blocks_for_rows(rows), kBlock, 0, st(), g.n0, rows, 1, Z0, y, (long long)h->s * g.nx);
+        launch(k_load<SI, double>, pt_blocks(ptmap(g.n0), rows), pt_threads(ptmap(g.n0)), 0, st(), ptmap(g.n0), (int)rows, 1,
+               Z0, y, (long long)h->s * g.nx);
         AAO_LAUNCH_CHECK();
         return AAO_OK;
     }

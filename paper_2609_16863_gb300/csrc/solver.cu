@@ -3,14 +3,18 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <string>
+#include <thread>
 #include <unordered_map>
+#include <vector>
 
 #include "handle.cuh"
 
 namespace aao {
 
-long long g_launches = 0;
+std::atomic<long long> g_launches{0};
+thread_local long long g_thread_launches = 0;
 bool g_prof_on = false;
 thread_local double g_bytes_hint = 0.0;
 static thread_local std::string g_last_error;
@@ -19,10 +23,13 @@ static thread_local std::string g_last_error;
 struct ProfState {
     std::string match;
     std::unordered_map<const void*, bool> hit;
+    std::unordered_map<const void*, std::string> names;
     std::vector<cudaEvent_t> ev;      // pool, pairs
     std::vector<double> bytes;
+    std::vector<const void*> kern;    // kernel of each slot
     size_t used = 0;
     std::string first_name;
+    std::string report;               // per-kernel table of the last profile
 };
 static ProfState g_prof;
 
@@ -33,6 +40,7 @@ int prof_begin_launch(const void* k, cudaStream_t st, double bytes) {
         const char* name = nullptr;
         h = cudaFuncGetName(&name, k) == cudaSuccess && name && std::strstr(name, g_prof.match.c_str());
         if (h && g_prof.first_name.empty()) g_prof.first_name = name;
+        if (h) g_prof.names[k] = name;
         cudaGetLastError();
         g_prof.hit[k] = h;
     } else {
@@ -50,6 +58,7 @@ int prof_begin_launch(const void* k, cudaStream_t st, double bytes) {
     }
     int slot = (int)g_prof.used++;
     g_prof.bytes.push_back(bytes);
+    g_prof.kern.push_back(k);
     cudaEventRecord(g_prof.ev[2 * slot], st);
     return slot;
 }
@@ -60,6 +69,7 @@ const char* get_error() { return g_last_error.c_str(); }
 
 // kappa_f / h^2 on every face from nodal kappa (all (n+2)^d nodes).
 __global__ void k_faces(Geo g, const double* kap, double* fx, double* fy, double* fz) {
+    pdl_prologue();
     const long long N0 = g.n0 + 2, N1 = g.n1 + 2;
     auto node = [&](long long I, long long J, long long K) -> double {
         return kap[I + N0 * (J + N1 * K)];
@@ -97,6 +107,7 @@ __global__ void k_faces(Geo g, const double* kap, double* fx, double* fy, double
 // W_{n,i} = v_n + tau sum_j a_ij V_{n,j}; one thread per node of the full grid.
 __global__ void k_grad_kappa(Geo g, int nt, Tab tab, double tau, const double* lam, const double* x,
                              double* grad) {
+    pdl_prologue();
     const long long N0 = g.n0 + 2, N1 = g.n1 + 2, N2 = g.d == 3 ? g.n2 + 2 : 1;
     long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= N0 * N1 * N2) return;
@@ -143,6 +154,7 @@ __global__ void k_grad_kappa(Geo g, int nt, Tab tab, double tau, const double* l
 }
 
 __global__ void k_outer_init(double* g, int m, const double* beta, int* flags) {
+    pdl_prologue();
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         for (int i = 0; i <= m; ++i) g[i] = i == 0 ? beta[0] : 0.0;
         flags[0] = 1;
@@ -157,6 +169,7 @@ struct SmallDev {
 };
 
 __global__ void k_pack_small(const double* resid, const int* flags, const double* beta, SmallDev* out) {
+    pdl_prologue();
     out->resid = resid[0];
     out->active = flags[0];
     out->its = flags[1];
@@ -374,7 +387,7 @@ static aao_status matvec_dev(Handle* h, const double* x, double* y, const double
 
 static aao_status norm_dev(Handle* h, const double* v, double* out) {
     const long long rows = h->nst / h->g.n0;
-    dim3 grid(h->nchunk_for(1, rows), 1);
+    dim3 grid(h->nchunk_for(1, rows * ((h->g.n0 + kWarp - 1) / kWarp)), 1);
     Red red = h->red;
     red.nchunk = grid.x;
     launch(k_norm<double>, grid, kBlock, 0, h->stream, h->g.n0, rows, 1, nullptr, v, h->nst, red, out, 1);
@@ -426,9 +439,10 @@ static aao_status fgmres(Handle* h, const double* b, double* x, int x0_given, in
         int total = 0;
         const double tol = h->opt.tol;
         Red red = h->red;
-        red.nchunk = h->nchunk_for(1, rows);
+        red.nchunk = h->nchunk_for(1, rows * ((n0 + kWarp - 1) / kWarp));
         dim3 rgrid(red.nchunk, 1);
-        const unsigned nb = blocks_for_rows(rows);
+        const PtMap pmo = ptmap(n0);
+        const unsigned nbp = pt_blocks(pmo, rows), ntp = pt_threads(pmo);
         while (true) {
             if (!std::isfinite(beta)) {
                 set_error("residual became non-finite");
@@ -441,7 +455,8 @@ static aao_status fgmres(Handle* h, const double* b, double* x, int x0_given, in
             }
             if (total >= h->opt.maxit) break;
             Vec<double> V0{h->V, nullptr, nst};
-            launch(k_scale_store<double, double>, nb, kBlock, 0, st, n0, rows, 1, nullptr, h->r, nst, h->beta, 0, V0);
+            launch(k_scale_store<double, double>, nbp, ntp, 0, st, pmo, (int)rows, 1, (const int*)nullptr, (const double*)h->r, nst,
+                   (const double*)h->beta, 0LL, V0);
             launch(k_outer_init, 1, 32, 0, st, h->gv, m, h->beta, h->flags);
             AAO_LAUNCH_CHECK();
             bool stop = false;
@@ -476,14 +491,15 @@ static aao_status fgmres(Handle* h, const double* b, double* x, int x0_given, in
                 }
                 if (!h->hsmall->active || total >= h->opt.maxit) break;
                 Vec<double> Vn{h->V + (long long)(k + 1) * nst, nullptr, nst};
-                launch(k_scale_store<double, double>, nb, kBlock, 0, st, n0, rows, 1, nullptr, h->w, nst,
+                launch(k_scale_store<double, double>, nbp, ntp, 0, st, pmo, (int)rows, 1, (const int*)nullptr, (const double*)h->w, nst,
                                                                      h->H + (k + 1) * m + k, 0, Vn);
                 AAO_LAUNCH_CHECK();
             }
             if (stop) break;
             launch(k_hess_solve, 1, 32, 0, st, 1, m, h->H, 0, h->gv, h->flags + 1, h->y, h->flags + 3);
             Vec<double> Zc{h->Z, nullptr, nst};
-            launch(k_combine<double, double>, nb, kBlock, 0, st, n0, rows, 1, Zc, nst, h->y, m, h->flags + 1, x, nst, 1);
+            launch(k_combine<double, double>, nbp, ntp, 0, st, pmo, (int)rows, 1, Zc, nst, (const double*)h->y, m,
+                   (const int*)(h->flags + 1), x, nst, 1);
             AAO_LAUNCH_CHECK();
             AAO_TRY(matvec_dev(h, x, h->r, b, transpose));
             AAO_TRY(norm_dev(h, h->r, h->beta));
@@ -594,6 +610,7 @@ aao_status aao_rk_profile_begin(const char* kernel_name) {
     g_prof.match = kernel_name;
     g_prof.hit.clear();
     g_prof.bytes.clear();
+    g_prof.kern.clear();
     g_prof.used = 0;
     g_prof.first_name.clear();
     g_prof_on = true;
@@ -604,18 +621,39 @@ aao_status aao_rk_profile_end(long long* launches, double* total_ms, double* tot
     g_prof_on = false;
     AAO_CUDA_TRY(cudaDeviceSynchronize());
     double ms = 0.0, by = 0.0;
+    struct Agg {
+        long long n = 0;
+        double ms = 0.0, bytes = 0.0;
+    };
+    std::unordered_map<const void*, Agg> agg;
     for (size_t i = 0; i < g_prof.used; ++i) {
         float t = 0.f;
         AAO_CUDA_TRY(cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]));
         ms += t;
         by += g_prof.bytes[i];
+        Agg& a = agg[g_prof.kern[i]];
+        a.n += 1;
+        a.ms += t;
+        a.bytes += g_prof.bytes[i];
+    }
+    g_prof.report.clear();
+    for (auto& kv : agg) {
+        char line[512];
+        std::snprintf(line, sizeof(line), "%s\t%lld\t%.6f\t%.1f\n", g_prof.names[kv.first].c_str(), kv.second.n,
+                      kv.second.ms, kv.second.bytes);
+        g_prof.report += line;
     }
     if (launches) *launches = (long long)g_prof.used;
     if (total_ms) *total_ms = ms;
     if (total_bytes) *total_bytes = by;
     g_prof.used = 0;
     g_prof.bytes.clear();
+    g_prof.kern.clear();
     return AAO_OK;
+}
+
+const char* aao_rk_profile_report(void) {
+    return g_prof.report.c_str();
 }
 
 aao_status aao_rk_setup(const aao_grid* grid, double tau, int nt, const aao_tableau* tab, const aao_options* opts,
@@ -840,12 +878,35 @@ aao_status aao_rk_solve_batched(int nprob, const aao_rk_handle* hs, const double
         set_error("bad batched arguments");
         return AAO_ERR_ARG;
     }
-    aao_status first = AAO_OK;
+    for (int p = 0; p < nprob; ++p)
+        if (!hs[p]) {
+            set_error("null handle in batch");
+            return AAO_ERR_ARG;
+        }
+    int dev = 0;
+    AAO_CUDA_TRY(cudaGetDevice(&dev));
+    // one host thread per problem: every problem's FGMRES loop (and its
+    // per-iteration convergence test) runs independently, so the GPU overlaps
+    // the latency-bound Schur sweeps of different problems.  Problems whose
+    // handles share a stream serialise on that stream.
+    std::vector<aao_status> st(nprob, AAO_OK);
+    std::vector<std::string> err(nprob);
+    std::vector<std::thread> th;
+    th.reserve(nprob);
     for (int p = 0; p < nprob; ++p) {
-        aao_status s = aao_rk_solve(hs[p], f[p], 0, u0[p], x[p], 0, infos ? &infos[p] : nullptr);
-        if (s != AAO_OK && first == AAO_OK) first = s;
+        th.emplace_back([&, p]() {
+            cudaSetDevice(dev);
+            st[p] = aao_rk_solve(hs[p], f[p], 0, u0[p], x[p], 0, infos ? &infos[p] : nullptr);
+            if (st[p] != AAO_OK) err[p] = get_error();
+        });
     }
-    return first;
+    for (auto& t : th) t.join();
+    for (int p = 0; p < nprob; ++p)
+        if (st[p] != AAO_OK) {
+            set_error("problem " + std::to_string(p) + ": " + err[p]);
+            return st[p];
+        }
+    return AAO_OK;
 }
 
 aao_status aao_rk_shifted_solve(aao_rk_handle hh, int stage, const double* b, double* x) {
