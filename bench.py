@@ -48,14 +48,63 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-preconditioner comparison solve")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--small", action="store_true", help="64x64, nt 16 (quick check; not a bench value)")
+    p.add_argument("--workload", default="fd2d_n256_radau3_nt128",
+                   choices=["fd2d_n256_radau3_nt128", "fd3d_n96_radau3_nt32", "fd3d_n96_gauss2_nt32", "batched64"],
+                   help="extra configurations (the default is the benchmark line)")
+    p.add_argument("--precond-case", action="store_true",
+                   help="small case for profiler captures: --steps applications of P_tilde (FP32) on the "
+                        "256x256 Radau IIA s=3 grid with 16 time steps; prints ms per application")
     return p.parse_args()
 
 
-def workload(small: bool):
+def workload(small: bool, name: str = WORKLOAD):
     import synth
     if small:
         return synth.workload_fp32_precond_2d(N=64, nt=16, s=3)
+    if name == "fd3d_n96_radau3_nt32":
+        return synth.workload_lowprec_3d(method="radau", s=3)
+    if name == "fd3d_n96_gauss2_nt32":
+        return synth.workload_lowprec_3d(method="gauss", s=2)
     return synth.workload_fp32_precond_2d()
+
+
+def batched_arm(args):
+    """64 uneven 2D problems in one aao_rk_solve_batched call (one stream each)."""
+    import torch
+    import synth
+    from paper_2609_16863_gb300 import Solver, _lib, radau_iia, solve_batched
+    dev = torch.device("cuda", 0)
+    ws = synth.workload_batched()
+    solvers, fs, us, xs = [], [], [], []
+    for w in ws:
+        st = torch.cuda.Stream(device=dev)
+        solvers.append(Solver(w.n, w.T, w.nt, tableau=radau_iia(w.s), prec_P=args.prec, inner_maxit=3,
+                              inner_tol=1e-3, tol=w.tol, stream=st.cuda_stream))
+        fs.append(torch.from_numpy(w.f).to(dev))
+        us.append(torch.from_numpy(w.u0).to(dev))
+        xs.append(torch.zeros(solvers[-1].n_st, dtype=torch.float64, device=dev))
+    for _ in range(args.warmup):
+        solve_batched(solvers, fs, us, xs)
+    torch.cuda.synchronize()
+    times = []
+    lat = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        infos = solve_batched(solvers, fs, us, xs)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        lat += [i.t_total_ms for i in infos]
+    t = float(np.median(times))
+    nst = sum(S.n_st for S in solvers)
+    its = [i.outer_its for i in infos]
+    line = {"metric": "batched uneven solves to 1e-8: wall time of the batch", "value": t, "unit": "s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": f"f64/{args.prec}",
+            "data": "synthetic", "config": {"workload": "batched64", "problems": len(ws), "n_st_total": nst},
+            "dofs_its_per_s": sum(S.n_st * i for S, i in zip(solvers, its)) / t,
+            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "outer_its_min_max": [min(its), max(its)], "all_converged": all(i.converged for i in infos)}
+    print(json.dumps(line), flush=True)
 
 
 def peaks():
@@ -173,10 +222,41 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def precond_case(args):
+    """P_tilde^{-1} r on a 256x256, s = 3, 16-step problem: the same kernels as the benchmark's
+    Schur sweep and batched Theta_tilde phase, small enough for a full profiler capture."""
+    import torch
+    import synth
+    from paper_2609_16863_gb300 import Solver, radau_iia
+    w = synth.workload_fp32_precond_2d(N=256, nt=16, s=3)
+    S = Solver(w.n, w.T, w.nt, tableau=radau_iia(3), prec_P=args.prec, inner_maxit=3, inner_tol=1e-3)
+    g = torch.Generator(device="cuda:0").manual_seed(5)
+    r = torch.randn(S.n_st, dtype=torch.float64, device="cuda:0", generator=g)
+    z = torch.zeros_like(r)
+    for _ in range(args.warmup):
+        S.precond_apply(r, z)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        S.precond_apply(r, z)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "precond_apply fd2d_n256_radau3_nt16", "prec": args.prec,
+                      "ms_per_apply": e0.elapsed_time(e1) / max(args.steps, 1)}))
+    S.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload == "batched64":
+        batched_arm(args)
+        return
+    if args.precond_case:
+        precond_case(args)
         return
     import torch
     import torch.distributed as dist
@@ -196,8 +276,9 @@ def main():
         if world > 1:
             dist.barrier()
 
-    w = workload(args.small)
-    common = dict(tableau=radau_iia(w.s), tol=w.tol, restart=20, maxit=100, stream=stream.cuda_stream)
+    w = workload(args.small, args.workload)
+    from paper_2609_16863_gb300.tableau import make as make_tableau
+    common = dict(tableau=make_tableau(w.method, w.s), tol=w.tol, restart=20, maxit=100, stream=stream.cuda_stream)
     S = Solver(w.n, w.T, w.nt, prec_P=args.prec, inner_maxit=3, inner_tol=1e-3, **common)
     f = torch.from_numpy(w.f).to(dev)
     u0 = torch.from_numpy(w.u0).to(dev)
@@ -313,7 +394,7 @@ def main():
     del Rb, Zb
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and args.workload == WORKLOAD:
         cpu = cpu_baseline(w, info.outer_its)
 
     if rank == 0:
@@ -321,7 +402,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": f"f64/{args.prec}", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "grid": [256, 256] if not args.small else list(w.n),
+                "config": {"workload": args.workload, "grid": list(w.n),
                            "nt": w.nt, "s": w.s, "n_st": S.n_st,
                            "precond": f"P_tilde {args.prec}, inner GMRES 3/1e-3, 3 V(2,2)-cycles",
                            "outer": "FP64 FGMRES(20), tol 1e-8",

@@ -180,6 +180,14 @@ aao_status aao_rk_adjoint_solve(aao_rk_handle h, const double* dJdx, double* lam
                                 const double* x_fwd, double* grad_f, double* grad_kappa,
                                 aao_info* info);
 
+/* grad_kappa (+)= -sum_{n,i} lambda_{V,n,i}^T (dK/dkappa) W_{n,i} over this handle's
+ * nt steps (FD only; device vectors of n_st, n_st and prod(n+2) values).  With
+ * accumulate != 0 the result is added to grad_kappa: a gradient over a long
+ * horizon can be summed window by window from forward states recomputed from
+ * checkpoints (each window a handle with nt = window length). */
+aao_status aao_rk_grad_kappa(aao_rk_handle h, const double* lambda, const double* x_fwd, double* grad_kappa,
+                             int accumulate);
+
 /* Solve nprob independent problems (each with its own handle, possibly of a
  * different grid, nt and s) in one call.  f[p], u0[p], x[p] as in
  * aao_rk_solve (device memory); infos may be NULL.  Returns the first

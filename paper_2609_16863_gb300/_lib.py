@@ -67,6 +67,7 @@ SIGNATURES = [
     ("aao_rk_solve", C.c_int, [H, P, C.c_int, P, P, C.c_int, C.POINTER(aao_info)]),
     ("aao_rk_solve_rhs", C.c_int, [H, P, P, C.c_int, C.POINTER(aao_info)]),
     ("aao_rk_adjoint_solve", C.c_int, [H, P, P, P, P, P, C.POINTER(aao_info)]),
+    ("aao_rk_grad_kappa", C.c_int, [H, P, P, P, C.c_int]),
     ("aao_rk_solve_batched", C.c_int, [C.c_int, C.POINTER(H), C.POINTER(P), C.POINTER(P), C.POINTER(P),
                                        C.POINTER(aao_info)]),
     ("aao_rk_shifted_solve", C.c_int, [H, C.c_int, P, P]),

@@ -58,7 +58,7 @@ class Solver:
                  lens=None, kappa=None, prec_P: str = "fp64", prec_Pint: Optional[str] = None,
                  tol: float = 1e-8, restart: int = 20, maxit: int = 100, inner_maxit: int = 0,
                  inner_tol: float = -1.0, mg_cycles: int = 3, mg_pre: int = 2, mg_post: int = 2,
-                 mg_omega: float = 0.8, stream=None):
+                 mg_omega: float = 0.8, disc: str = "fd", cheb_steps: int = 20, stream=None):
         self._lib = _lib.lib()
         self.n = tuple(int(v) for v in n)
         self.dim = len(self.n)
@@ -72,7 +72,7 @@ class Solver:
         for a in range(3):
             g.n[a] = self.n[a] if a < self.dim else 1
             g.len[a] = (lens[a] if lens is not None else 1.0) if a < self.dim else 1.0
-        g.disc = _lib.DISC["fd"]
+        g.disc = _lib.DISC[disc]
         self._kappa = kappa     # keep alive until set-up copied it
         g.kappa = _ptr(kappa)
         t = _lib.aao_tableau()
@@ -87,6 +87,7 @@ class Solver:
         o.tol, o.restart, o.maxit = tol, restart, maxit
         o.inner_maxit, o.inner_tol = inner_maxit, inner_tol
         o.mg_cycles, o.mg_pre, o.mg_post, o.mg_omega = mg_cycles, mg_pre, mg_post, mg_omega
+        o.cheb_steps = cheb_steps
         o.prec_P = _lib.PREC[prec_P]
         o.prec_Pint = _lib.PREC[prec_Pint if prec_Pint is not None else prec_P]
         o.stream = stream
@@ -170,6 +171,11 @@ class Solver:
                                                   _ptr(grad_kappa), C.byref(info)),
                    allow=(-4,) if allow_not_converged else ())
         return lam, Info.from_c(info)
+
+
+    def grad_kappa(self, lam, x_fwd, out, accumulate=False):
+        _lib.check(self._lib.aao_rk_grad_kappa(self.h, _ptr(lam), _ptr(x_fwd), _ptr(out), int(accumulate)))
+        return out
 
 
 def solve_batched(solvers, fs, u0s, xs):

@@ -156,11 +156,14 @@ inline PtMap ptmap(int n0) {
     m.rpc = p >= 256 ? 1 : 256 / p;
     return m;
 }
-inline unsigned int pt_blocks(const PtMap& m, long long rows) {
-    long long b = (rows + m.rpc - 1) / m.rpc;
-    return (unsigned int)(b < 1 ? 1 : b);
+// Launch geometry: block (n0p, rpc) threads, grid (ceil(R / rpc), B): thread x is
+// the column, thread y the row within the CTA, block y the batch item, so the
+// kernels need no integer division to find their point.
+inline dim3 pt_grid(const PtMap& m, long long R, int B) {
+    long long bx = (R + m.rpc - 1) / m.rpc;
+    return dim3((unsigned int)(bx < 1 ? 1 : bx), (unsigned int)(B < 1 ? 1 : B), 1);
 }
-inline unsigned int pt_threads(const PtMap& m) { return (unsigned int)(m.rpc * m.n0p); }
+inline dim3 pt_block(const PtMap& m) { return dim3((unsigned int)m.n0p, (unsigned int)m.rpc, 1); }
 
 // Row coordinates of the calling thread for B items of R rows each.
 struct PtPos {
@@ -168,14 +171,13 @@ struct PtPos {
     long long row;
     bool valid;
 };
-__device__ __forceinline__ PtPos pt_pos(const PtMap& m, int B, int R, const int* active) {
+__device__ __forceinline__ PtPos pt_pos(const PtMap& m, int B, long long R, const int* active) {
     PtPos q;
-    q.lrow = threadIdx.x / m.n0p;
-    q.c0 = threadIdx.x % m.n0p;
-    long long w = (long long)blockIdx.x * m.rpc + q.lrow;
-    q.valid = w < (long long)B * R;
-    q.b = q.valid ? (int)(w / R) : 0;
-    q.row = q.valid ? w % R : 0;
+    q.lrow = threadIdx.y;
+    q.c0 = threadIdx.x;
+    q.b = blockIdx.y;
+    q.row = (long long)blockIdx.x * m.rpc + threadIdx.y;
+    q.valid = q.row < R && q.b < B;
     if (q.valid && active && !active[q.b]) q.valid = false;
     return q;
 }
@@ -189,9 +191,10 @@ __device__ __forceinline__ void pt_store(S* out_row, float* out_sc, const PtMap&
         float v = 0.f;
         if (valid && c0 < m.n0) v = (float)f(c0);
         float a = warp_max(fabsf(v));
-        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = a;
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        if ((tid & 31) == 0) wmax[tid >> 5] = a;
         __syncthreads();
-        const int wpr = m.n0p >> 5, first = (threadIdx.x / m.n0p) * wpr;
+        const int wpr = m.n0p >> 5, first = threadIdx.y * wpr;
         float mx = 0.f;
         for (int i = 0; i < wpr; ++i) mx = fmaxf(mx, wmax[first + i]);
         int e = 0;
@@ -233,6 +236,18 @@ struct Geo {
     double hx2, hy2, hz2;   // 1/h^2 per axis
 };
 
+// (j, k) of a grid row without 64-bit division (2D: k = 0).
+__device__ __forceinline__ void row_jk(const Geo& g, long long row, int& j, int& k) {
+    if (g.d == 2) {
+        j = (int)row;
+        k = 0;
+    } else {
+        const int r = (int)row;
+        k = r / g.n1;
+        j = r - k * g.n1;
+    }
+}
+
 template <class T> struct Faces {
     const T* fx = nullptr;
     const T* fy = nullptr;
@@ -270,6 +285,86 @@ __device__ __forceinline__ typename PT<S>::A fd_K(const View<S>& u, const Geo& g
         }
     }
     return out;
+}
+
+// ---------------------------------------------------------------------------
+// Q1 finite elements on the tensor vertex mesh (Sec. 5): M = (x)_a M1_a and
+// K = sum_a (x)_{b != a} M1_b (x) K1_a with the 1D linear-element matrices
+// M1 = h/6 tridiag(1, 4, 1), K1 = 1/h tridiag(-1, 2, -1) on the interior nodes.
+// m[a][e], k[a][e] hold the 1D coefficients of offset e - 1 along axis a.
+// ---------------------------------------------------------------------------
+template <class T> struct Q1 {
+    T m[3][3];
+    T k[3][3];
+};
+
+// alpha_m (M u)_P + alpha_k (K u)_P for the Q1 stencils.
+template <class S, class T>
+__device__ __forceinline__ typename PT<S>::A q1_apply(const View<S>& u, const Geo& g, const Q1<T>& q, long long row,
+                                                      int j, int k, int c, typename PT<S>::A am,
+                                                      typename PT<S>::A ak) {
+    using A = typename PT<S>::A;
+    A acc = A(0);
+    const int zlo = g.d == 3 ? -1 : 0, zhi = g.d == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+        int kk = k + dz;
+        if (kk < 0 || kk >= g.n2) continue;
+        const A mz = g.d == 3 ? A(q.m[2][dz + 1]) : A(1), kz = g.d == 3 ? A(q.k[2][dz + 1]) : A(0);
+        for (int dy = -1; dy <= 1; ++dy) {
+            int jj = j + dy;
+            if (jj < 0 || jj >= g.n1) continue;
+            const A my = A(q.m[1][dy + 1]), ky = A(q.k[1][dy + 1]);
+            long long rr = row + dy + (long long)dz * g.n1;
+            for (int dx = -1; dx <= 1; ++dx) {
+                int cc = c + dx;
+                if (cc < 0 || cc >= g.n0) continue;
+                const A mx = A(q.m[0][dx + 1]), kx = A(q.k[0][dx + 1]);
+                A kcoef = kx * my * mz + mx * ky * mz;
+                if (g.d == 3) kcoef += mx * my * kz;
+                acc += (am * mx * my * mz + ak * kcoef) * A(u.at(rr, cc));
+            }
+        }
+    }
+    return acc;
+}
+
+template <class T> inline Q1<T> make_q1(const Geo& g, double hx, double hy, double hz) {
+    Q1<T> q;
+    const double h[3] = {hx, hy, hz};
+    for (int a = 0; a < 3; ++a) {
+        q.m[a][0] = T(h[a] / 6.0);
+        q.m[a][1] = T(4.0 * h[a] / 6.0);
+        q.m[a][2] = T(h[a] / 6.0);
+        q.k[a][0] = T(-1.0 / h[a]);
+        q.k[a][1] = T(2.0 / h[a]);
+        q.k[a][2] = T(-1.0 / h[a]);
+    }
+    (void)g;
+    return q;
+}
+
+// Spatial operator of the fine grid as the stage kernels see it: FD (faces,
+// M = I) or Q1 (tensor stencils for M and K).
+template <class T> struct SpaceOp {
+    int q1 = 0;
+    Q1<T> q;
+    Faces<T> faces;
+};
+
+template <class S, class T>
+__device__ __forceinline__ typename PT<S>::A op_K(const View<S>& u, const Geo& g, const SpaceOp<T>& op,
+                                                  long long row, int j, int k, int c) {
+    using A = typename PT<S>::A;
+    if (op.q1) return q1_apply(u, g, op.q, row, j, k, c, A(0), A(1));
+    return fd_K(u, g, op.faces, row, j, k, c);
+}
+
+template <class S, class T>
+__device__ __forceinline__ typename PT<S>::A op_M(const View<S>& u, const Geo& g, const SpaceOp<T>& op,
+                                                  long long row, int j, int k, int c) {
+    using A = typename PT<S>::A;
+    if (op.q1) return q1_apply(u, g, op.q, row, j, k, c, A(1), A(0));
+    return A(u.at(row, c));
 }
 
 // Diagonal of K at a point.

@@ -80,6 +80,8 @@ struct Handle {
     double* d_LDb = nullptr;       // s*s: row i holds (L D)_{ji}, j > i
     Faces<double> faces64;         // nullptr members for kappa == 1
     int has_kappa = 0;
+    int q1 = 0;                    // Q1 finite elements (else finite differences, M = I)
+    Q1<double> q1d;
 
     // outer FGMRES workspace
     int m = 0;                     // restart

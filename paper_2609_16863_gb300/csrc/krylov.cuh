@@ -63,14 +63,14 @@ __global__ void __launch_bounds__(kBlock) k_norm(int n0, long long rows, int B, 
     if (active && !active[b]) return;
     const SR* x = src + (long long)b * bs;
     const int w = threadIdx.x >> 5, lane = lane_id();
-    const int spr = (n0 + kWarp - 1) / kWarp;
-    const long long nseg = rows * spr;
+    const unsigned spr = (n0 + kWarp - 1) / kWarp;
+    const unsigned nseg = (unsigned)(rows * spr);   // < 2^32 segments (checked on the host)
     SR acc = SR(0);
-    for (long long g = (long long)blockIdx.x * kWarpsPerBlock + w; g < nseg; g += (long long)red.nchunk * kWarpsPerBlock) {
-        long long r = g / spr;
-        int c = (int)(g % spr) * kWarp + lane;
+    for (unsigned g = blockIdx.x * kWarpsPerBlock + w; g < nseg; g += red.nchunk * kWarpsPerBlock) {
+        const unsigned r = g / spr;
+        int c = (int)(g - r * spr) * kWarp + lane;
         if (c < n0) {
-            SR v = x[r * n0 + c];
+            SR v = x[(long long)r * n0 + c];
             acc += v * v;
         }
     }
@@ -92,14 +92,14 @@ __global__ void __launch_bounds__(kBlock) k_mgs(int n0, long long rows, int B, c
     View<SV> vn = dot ? view_of(Vn, b, 0, n0) : View<SV>{nullptr, nullptr, n0};
     A h = upd ? (A)hp[(long long)b * hstride] : A(0);
     const int wi = threadIdx.x >> 5, lane = lane_id();
-    const int spr = (n0 + kWarp - 1) / kWarp;
-    const long long nseg = rows * spr;
+    const unsigned spr = (n0 + kWarp - 1) / kWarp;
+    const unsigned nseg = (unsigned)(rows * spr);   // < 2^32 segments (checked on the host)
     A acc = A(0);
-    for (long long g = (long long)blockIdx.x * kWarpsPerBlock + wi; g < nseg; g += (long long)red.nchunk * kWarpsPerBlock) {
-        long long r = g / spr;
-        int c = (int)(g % spr) * kWarp + lane;
+    for (unsigned g = blockIdx.x * kWarpsPerBlock + wi; g < nseg; g += red.nchunk * kWarpsPerBlock) {
+        const unsigned r = g / spr;
+        int c = (int)(g - r * spr) * kWarp + lane;
         if (c < n0) {
-            long long i = r * n0 + c;
+            long long i = (long long)r * n0 + c;
             A x = w[i];
             if (upd) {
                 x -= h * vp.at(r, c);
@@ -269,22 +269,23 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_combine(PtMap pm, int rows, i
 // ---------------------------------------------------------------------------
 template <class SZ, class A>
 __global__ void __launch_bounds__(kPtMaxThreads) k_theta(Geo g, PtMap pm, int B, const int* active, Vec<SZ> Z, A* wv,
-                                                long long wbs, int s, const double* coef, A tau, Faces<A> faces) {
+                                                long long wbs, int s, const double* coef, A tau, SpaceOp<A> sop) {
     pdl_prologue();
     PtPos q = pt_pos(pm, B, g.R, active);
     if (!q.valid) return;
     const long long row = q.row;
-    const int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    int j, k;
+    row_jk(g, row, j, k);
     A* out = wv + (long long)q.b * wbs + row * g.n0;
     for (int c = q.c0; c < g.n0; c += pm.n0p) {
         A kz[kMaxS];
         for (int i = 0; i < s; ++i) {
             View<SZ> zi = view_of(Z, q.b, (long long)i * g.nx, g.n0);
-            kz[i] = (A)fd_K(zi, g, faces, row, j, k, c);
+            kz[i] = (A)op_K(zi, g, sop, row, j, k, c);
         }
         for (int i = 0; i < s; ++i) {
             View<SZ> zi = view_of(Z, q.b, (long long)i * g.nx, g.n0);
-            A acc = (A)zi.at(row, c);
+            A acc = (A)op_M(zi, g, sop, row, j, k, c);
             for (int jj = 0; jj < s; ++jj) acc += tau * (A)coef[i * s + jj] * kz[jj];
             out[(long long)i * g.nx + c] = acc;
         }
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_theta(Geo g, PtMap pm, int B,
 template <class SV, class SZ>
 __global__ void __launch_bounds__(kPtMaxThreads) k_rana_rhs(Geo g, PtMap pm, int B, const int* active, Vec<SV> V, int stage,
                                                    Vec<SZ> Z, int s, const double* coef, typename PT<SZ>::A tau,
-                                                   Faces<typename PT<SZ>::A> faces, Vec<SZ> out) {
+                                                   SpaceOp<typename PT<SZ>::A> sop, Vec<SZ> out) {
     pdl_prologue();
     using A = typename PT<SZ>::A;
     PtPos q = pt_pos(pm, B, g.R, active);
@@ -303,7 +304,8 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_rana_rhs(Geo g, PtMap pm, int
         if (!q.valid) return;
     }
     const long long row = q.row;
-    const int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    int j, k;
+    row_jk(g, row, j, k);
     View<SV> v = view_of(V, q.b, (long long)stage * g.nx, g.n0);
     SZ* o; float* osc;
     row_store_ptrs(out, q.b, 0, row, g.n0, o, osc);
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_rana_rhs(Geo g, PtMap pm, int
             const double cf = coef[jj];
             if (cf != 0.0) {
                 View<SZ> zj = view_of(Z, q.b, (long long)jj * g.nx, g.n0);
-                acc -= tau * (A)cf * (A)fd_K(zj, g, faces, row, j, k, c);
+                acc -= tau * (A)cf * (A)op_K(zj, g, sop, row, j, k, c);
             }
         }
         return acc;
@@ -367,14 +369,15 @@ static __global__ void k_step_add(StepPtrs* sp, int d) {
 
 // t_i = K z_{v,n} for every stage i (the e (x) K z_{v,n} right-hand side).
 template <class A>
-__global__ void __launch_bounds__(kBlock) k_schur_rhs(Geo g, int s, const StepPtrs* sp, A* t, Faces<A> faces) {
+__global__ void __launch_bounds__(kBlock) k_schur_rhs(Geo g, int s, const StepPtrs* sp, A* t, SpaceOp<A> sop) {
     pdl_prologue();
     long long row = gwarp();
     if (row >= g.R) return;
-    int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    int j, k;
+    row_jk(g, row, j, k);
     View<double> z{sp->z + (long long)sp->n * g.nx, nullptr, g.n0};
     for (int c = lane_id(); c < g.n0; c += kWarp) {
-        A v = (A)fd_K(z, g, faces, row, j, k, c);
+        A v = (A)op_K(z, g, sop, row, j, k, c);
         for (int i = 0; i < s; ++i) t[(long long)i * g.nx + row * g.n0 + c] = v;
     }
 }
@@ -425,11 +428,12 @@ __global__ void k_schurT_rhs(long long nx, int s, const StepPtrs* sp, const doub
 // u_n = r_{v,n} + u_{n+1} - tau sum_i K q_i   (q flat, s*nx, type A).
 template <class A>
 __global__ void __launch_bounds__(kBlock) k_schurT_update(Geo g, int s, const StepPtrs* sp, const A* q,
-                                                          double tau, Faces<A> faces) {
+                                                          double tau, SpaceOp<A> sop) {
     pdl_prologue();
     long long row = gwarp();
     if (row >= g.R) return;
-    int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    int j, k;
+    row_jk(g, row, j, k);
     const int n = sp->n;
     const double* rvn = sp->r + (long long)n * g.nx;
     const double* un1 = sp->z + (long long)(n + 1) * g.nx;
@@ -439,7 +443,7 @@ __global__ void __launch_bounds__(kBlock) k_schurT_update(Geo g, int s, const St
     for (int c = lane_id(); c < g.n0; c += kWarp) {
         long long p = row * g.n0 + c;
         A acc = A(0);
-        for (int i = 0; i < s; ++i) acc += (A)fd_K(qs[i], g, faces, row, j, k, c);
+        for (int i = 0; i < s; ++i) acc += (A)op_K(qs[i], g, sop, row, j, k, c);
         un[p] = (double)((A)rvn[p] + (A)un1[p] - (A)tau * acc);
     }
 }
@@ -465,6 +469,207 @@ __global__ void k_convert(const SI* in, SO* out, long long n) {
     if (i < n) out[i] = (SO)in[i];
 }
 
+struct Tab {
+    int s;
+    double A[kMaxS * kMaxS];
+    double b[kMaxS];
+};
+
+// ---------------------------------------------------------------------------
+// Q1 pieces of the Schur substitution: M applied inside the right-hand sides,
+// and M^{-1} by Chebyshev semi-iteration with Jacobi splitting (Sec. 5: 20
+// steps), batched over blocks of n_x values.
+// ---------------------------------------------------------------------------
+// g_0 = r_{v,0};  g_{n+1} = r_{v,n+1} + tau M (sum_i b_i zV_{n,i})   (point-mapped over (nt+1) blocks)
+template <class A>
+__global__ void __launch_bounds__(kPtMaxThreads) k_schur_g_q1(Geo g, PtMap pm, int nt, int s, const double* r,
+                                                              const double* zV, const double* bw, double tau,
+                                                              Q1<A> q, A* wbuf) {
+    pdl_prologue();
+    PtPos p = pt_pos(pm, nt + 1, g.R, nullptr);
+    if (!p.valid) return;
+    const long long row = p.row;
+    int j, k;
+    row_jk(g, row, j, k);
+    const int n = p.b;
+    for (int c = p.c0; c < g.n0; c += pm.n0p) {
+        const long long idx = (long long)n * g.nx + row * g.n0 + c;
+        if (n == 0) {
+            wbuf[idx] = (A)r[idx];
+            continue;
+        }
+        A acc = A(0);
+        for (int i = 0; i < s; ++i) {
+            View<double> zi{zV + ((long long)(n - 1) * s + i) * g.nx, nullptr, g.n0};
+            acc += (A)bw[i] * (A)q1_apply(zi, g, q, row, j, k, c, 1.0, 0.0);
+        }
+        wbuf[idx] = (A)r[idx] + (A)tau * acc;
+    }
+}
+
+// Chebyshev set-up: x = 0, r = g, d = D^{-1} g / theta  (flat, n values)
+template <class A>
+__global__ void k_cheb_init(long long n, const A* g, A dinv_theta, A* x, A* r, A* d) {
+    pdl_prologue();
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    x[i] = A(0);
+    r[i] = g[i];
+    d[i] = dinv_theta * g[i];
+}
+
+// x += d;  r -= M d   (B blocks of n_x)
+template <class A>
+__global__ void __launch_bounds__(kPtMaxThreads) k_cheb_a(Geo g, PtMap pm, int B, Q1<A> q, const A* d, A* x, A* r) {
+    pdl_prologue();
+    PtPos p = pt_pos(pm, B, g.R, nullptr);
+    if (!p.valid) return;
+    const long long row = p.row;
+    int j, k;
+    row_jk(g, row, j, k);
+    View<A> dv{d + (long long)p.b * g.nx, nullptr, g.n0};
+    for (int c = p.c0; c < g.n0; c += pm.n0p) {
+        const long long idx = (long long)p.b * g.nx + row * g.n0 + c;
+        x[idx] += d[idx];
+        r[idx] -= q1_apply(dv, g, q, row, j, k, c, A(1), A(0));
+    }
+}
+
+// d = c1 d + c2 D^{-1} r
+template <class A>
+__global__ void k_cheb_b(long long n, A c1, A c2dinv, const A* r, A* d) {
+    pdl_prologue();
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    d[i] = c1 * d[i] + c2dinv * r[i];
+}
+
+// t_{n,i} = r_{V,n,i} + tau b_i (M z_{v,n+1})_  (Q1, point-mapped over nt blocks)
+template <class A>
+__global__ void __launch_bounds__(kPtMaxThreads) k_schurT_vrhs_q1(Geo g, PtMap pm, int nt, int s, const double* rV,
+                                                                  const double* zv, const double* bw, double tau,
+                                                                  Q1<A> q, A* t) {
+    pdl_prologue();
+    PtPos p = pt_pos(pm, nt, g.R, nullptr);
+    if (!p.valid) return;
+    const long long row = p.row;
+    int j, k;
+    row_jk(g, row, j, k);
+    const int n = p.b;
+    View<double> zn{zv + (long long)(n + 1) * g.nx, nullptr, g.n0};
+    for (int c = p.c0; c < g.n0; c += pm.n0p) {
+        A mz = (A)q1_apply(zn, g, q, row, j, k, c, 1.0, 0.0);
+        for (int i = 0; i < s; ++i) {
+            const long long idx = ((long long)n * s + i) * g.nx + row * g.n0 + c;
+            t[idx] = (A)rV[idx] + (A)tau * (A)bw[i] * mz;
+        }
+    }
+}
+
+// FP64 all-at-once matvec for Q1 (M and K both 3^d-point), same row structure
+// as k_matvec; transposes use M^T = M, K^T = K.
+static __global__ void __launch_bounds__(kBlock) k_matvec_q1(Geo g, int nt, Tab tab, double tau, Q1<double> q,
+                                                             const double* x, double* y, const double* rhs,
+                                                             int transpose) {
+    pdl_prologue();
+    long long w = gwarp();
+    if (w >= (long long)(nt + 1) * g.R) return;
+    int n = (int)(w / g.R);
+    long long row = w % g.R;
+    int j, k;
+    row_jk(g, row, j, k);
+    const int s = tab.s;
+    const long long nx = g.nx;
+    const long long voff = (long long)(nt + 1) * nx;
+    const int lane = lane_id();
+    if (n == nt) {   // y_{v,0} = M v_0 (forward) or y_{v,nt} = M l_{v,nt} (transpose)
+        long long base = transpose ? (long long)nt * nx : 0;
+        View<double> v{x + base, nullptr, g.n0};
+        for (int c = lane; c < g.n0; c += kWarp) {
+            long long p = base + row * g.n0 + c;
+            double a = q1_apply(v, g, q, row, j, k, c, 1.0, 0.0);
+            y[p] = rhs ? rhs[p] - a : a;
+        }
+        return;
+    }
+    View<double> vn{x + (long long)n * nx, nullptr, g.n0};
+    View<double> vn1{x + (long long)(n + 1) * nx, nullptr, g.n0};
+    View<double> Vs[kMaxS];
+    for (int i = 0; i < s; ++i) Vs[i] = View<double>{x + voff + ((long long)n * s + i) * nx, nullptr, g.n0};
+    for (int c = lane; c < g.n0; c += kWarp) {
+        long long p = row * g.n0 + c;
+        double KV[kMaxS], MV[kMaxS];
+        for (int i = 0; i < s; ++i) {
+            KV[i] = q1_apply(Vs[i], g, q, row, j, k, c, 0.0, 1.0);
+            MV[i] = q1_apply(Vs[i], g, q, row, j, k, c, 1.0, 0.0);
+        }
+        if (!transpose) {
+            double acc = q1_apply(vn1, g, q, row, j, k, c, 1.0, 0.0) - q1_apply(vn, g, q, row, j, k, c, 1.0, 0.0);
+            for (int i = 0; i < s; ++i) acc -= tau * tab.b[i] * MV[i];
+            long long yi = (long long)(n + 1) * nx + p;
+            y[yi] = rhs ? rhs[yi] - acc : acc;
+            double Kv = q1_apply(vn, g, q, row, j, k, c, 0.0, 1.0);
+            for (int i = 0; i < s; ++i) {
+                double a = MV[i] + Kv;
+                for (int qq = 0; qq < s; ++qq) a += tau * tab.A[i * s + qq] * KV[qq];
+                long long yv = voff + ((long long)n * s + i) * nx + p;
+                y[yv] = rhs ? rhs[yv] - a : a;
+            }
+        } else {
+            double Mln1 = q1_apply(vn1, g, q, row, j, k, c, 1.0, 0.0);
+            double acc = q1_apply(vn, g, q, row, j, k, c, 1.0, 0.0) - Mln1;
+            for (int i = 0; i < s; ++i) acc += KV[i];
+            long long yi = (long long)n * nx + p;
+            y[yi] = rhs ? rhs[yi] - acc : acc;
+            for (int i = 0; i < s; ++i) {
+                double a = MV[i] - tau * tab.b[i] * Mln1;
+                for (int qq = 0; qq < s; ++qq) a += tau * tab.A[qq * s + i] * KV[qq];
+                long long yv = voff + ((long long)n * s + i) * nx + p;
+                y[yv] = rhs ? rhs[yv] - a : a;
+            }
+        }
+    }
+}
+
+// rhs = [M u0 ; 0 ; M f_{n,i}] for Q1 (point-mapped over nt*s + 2 blocks: block 0 = v_0,
+// block 1 = the zero v blocks, blocks >= 2 the stage blocks)
+static __global__ void __launch_bounds__(kPtMaxThreads) k_rhs_q1(Geo g, PtMap pm, int nt, int s, const double* f,
+                                                                 int f_time_dep, const double* u0, Q1<double> q,
+                                                                 double* out) {
+    pdl_prologue();
+    const int nblk = nt * s + 2;
+    PtPos p = pt_pos(pm, nblk, g.R, nullptr);
+    if (!p.valid) return;
+    const long long row = p.row, nx = g.nx;
+    int j, k;
+    row_jk(g, row, j, k);
+    for (int c = p.c0; c < g.n0; c += pm.n0p) {
+        const long long pi = row * g.n0 + c;
+        if (p.b == 0) {
+            View<double> u{u0, nullptr, g.n0};
+            out[pi] = q1_apply(u, g, q, row, j, k, c, 1.0, 0.0);
+        } else if (p.b == 1) {
+            for (int n = 1; n <= nt; ++n) out[(long long)n * nx + pi] = 0.0;
+        } else {
+            const long long blk = p.b - 2;
+            View<double> u{f_time_dep ? f + blk * nx : f, nullptr, g.n0};
+            out[(long long)(nt + 1) * nx + blk * nx + pi] = q1_apply(u, g, q, row, j, k, c, 1.0, 0.0);
+        }
+    }
+}
+
+// gf = M sum_{n,i} lambda_{V,n,i}  (Q1; the plain sum is formed by k_grad_f first, in place)
+static __global__ void __launch_bounds__(kPtMaxThreads) k_apply_M_q1(Geo g, PtMap pm, Q1<double> q, const double* in,
+                                                                     double* out) {
+    pdl_prologue();
+    PtPos p = pt_pos(pm, 1, g.R, nullptr);
+    if (!p.valid) return;
+    int j, k;
+    row_jk(g, p.row, j, k);
+    View<double> u{in, nullptr, g.n0};
+    for (int c = p.c0; c < g.n0; c += pm.n0p) out[p.row * g.n0 + c] = q1_apply(u, g, q, p.row, j, k, c, 1.0, 0.0);
+}
+
 // ---------------------------------------------------------------------------
 // FP64 all-at-once matvec (FD, M = I), one warp per (time block n, row):
 //   y_{v,0}   = v_0
@@ -475,11 +680,6 @@ __global__ void k_convert(const SI* in, SO* out, long long n) {
 //   y_{V,n,i} = l_{V,n,i} - tau b_i l_{v,n+1} + tau sum_j a_ji K l_{V,n,j}.
 // rhs != nullptr gives y = rhs - (A x).  Warps with n == nt handle block v_0 / v_nt.
 // ---------------------------------------------------------------------------
-struct Tab {
-    int s;
-    double A[kMaxS * kMaxS];
-    double b[kMaxS];
-};
 
 static __global__ void __launch_bounds__(kBlock) k_matvec(Geo g, int nt, Tab tab, double tau, Faces<double> faces,
                                                    const double* x, double* y, const double* rhs, int transpose) {
@@ -488,7 +688,8 @@ static __global__ void __launch_bounds__(kBlock) k_matvec(Geo g, int nt, Tab tab
     if (w >= (long long)(nt + 1) * g.R) return;
     int n = (int)(w / g.R);
     long long row = w % g.R;
-    int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    int j, k;
+    row_jk(g, row, j, k);
     const int s = tab.s;
     const long long nx = g.nx;
     const long long voff = (long long)(nt + 1) * nx;

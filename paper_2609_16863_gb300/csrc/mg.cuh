@@ -148,12 +148,14 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_smooth2(LevelOp<S> op, PtMap 
         if (!q.valid) return;
     }
     const long long row = q.row;
-    const int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    int j, k;
+    row_jk(g, row, j, k);
     View<S> bb = view_of(bv, q.b, 0, g.n0);
     const bool has = xin.d != nullptr;
     View<S> xx = has ? view_of(xin, q.b, 0, g.n0) : View<S>{nullptr, nullptr, g.n0};
     auto x1 = [&](long long rr, int cc) -> A {
-        const int jj = (int)(rr % g.n1), kk = (int)(rr / g.n1);
+        int jj, kk;
+    row_jk(g, rr, jj, kk);
         if (!has) return omega * bb.at(rr, cc) / level_diag(op, rr, jj, kk, cc);
         A Au, dg;
         level_apply(op, xx, rr, jj, kk, cc, Au, dg);
@@ -182,7 +184,8 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_resid_restrict(LevelOp<S> op,
         if (!q.valid) return;
     }
     const long long row = q.row;
-    const int J = (int)(row % gc.n1), Kc = (int)(row / gc.n1);
+    int J, Kc;
+    row_jk(gc, row, J, Kc);
     View<S> bb = view_of(bv, q.b, 0, gf.n0);
     const bool has = xv.d != nullptr;
     View<S> xx = has ? view_of(xv, q.b, 0, gf.n0) : View<S>{nullptr, nullptr, gf.n0};
@@ -230,7 +233,8 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_smooth(LevelOp<S> op, PtMap p
         if (!q.valid) return;
     }
     const long long row = q.row;
-    const int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    int j, k;
+    row_jk(g, row, j, k);
     View<S> bb = view_of(bv, q.b, 0, g.n0);
     S* out; float* osc;
     row_store_ptrs(xout, q.b, 0, row, g.n0, out, osc);
@@ -263,7 +267,8 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_residual(LevelOp<S> op, PtMap
         if (!q.valid) return;
     }
     const long long row = q.row;
-    const int j = (int)(row % g.n1), k = (int)(row / g.n1);
+    int j, k;
+    row_jk(g, row, j, k);
     View<S> xx = view_of(xv, q.b, 0, g.n0);
     View<S> bb = view_of(bv, q.b, 0, g.n0);
     S* out; float* osc;
@@ -286,7 +291,8 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_restrict(Geo gf, Geo gc, PtMa
         if (!q.valid) return;
     }
     const long long row = q.row;
-    const int J = (int)(row % gc.n1), Kc = (int)(row / gc.n1);
+    int J, Kc;
+    row_jk(gc, row, J, Kc);
     View<S> rr = view_of(rv, q.b, 0, gf.n0);
     S* out; float* osc;
     row_store_ptrs(bcv, q.b, 0, row, gc.n0, out, osc);
@@ -341,7 +347,8 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_prolong_add(Geo gf, Geo gc, P
         if (!q.valid) return;
     }
     const long long row = q.row;
-    const int j = (int)(row % gf.n1), k = (int)(row / gf.n1);
+    int j, k;
+    row_jk(gf, row, j, k);
     View<S> xc = view_of(xcv, q.b, 0, gc.n0);
     const bool has_in = xin.d != nullptr;
     View<S> xi = has_in ? view_of(xin, q.b, 0, gf.n0) : View<S>{nullptr, nullptr, gf.n0};
@@ -380,13 +387,15 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_prolong_smooth(LevelOp<S> op,
         if (!q.valid) return;
     }
     const long long row = q.row;
-    const int j = (int)(row % gf.n1), k = (int)(row / gf.n1);
+    int j, k;
+    row_jk(gf, row, j, k);
     View<S> xc = view_of(xcv, q.b, 0, gc.n0);
     View<S> bb = view_of(bv, q.b, 0, gf.n0);
     const bool has = xin.d != nullptr;
     View<S> xi = has ? view_of(xin, q.b, 0, gf.n0) : View<S>{nullptr, nullptr, gf.n0};
     auto xp = [&](long long rr, int cc) -> A {
-        const int jj = (int)(rr % gf.n1), kk = (int)(rr / gf.n1);
+        int jj, kk;
+    row_jk(gf, rr, jj, kk);
         int Jx[2], Jy[2], Jz[2] = {0, 0};
         float wx[2], wy[2], wz[2] = {1.f, 0.f};
         int mx = interp_1d(cc, gc.n0, Jx, wx);
@@ -544,6 +553,24 @@ static __global__ void k_galerkin(FineDesc fd, Geo gc, double* out) {
     for (int q = 0; q < ncoef; ++q) out[(long long)q * gc.nx + p] = acc[q];
 }
 
+// Q1: the fine-level operator M + c K as a stored FP64 3^d-point stencil.
+static __global__ void k_q1_stencil(Geo g, Q1<double> q, double c, double* out) {
+    pdl_prologue();
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.nx) return;
+    const int zlo = g.d == 3 ? -1 : 0, zhi = g.d == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const double mx = q.m[0][dx + 1], my = q.m[1][dy + 1], mz = g.d == 3 ? q.m[2][dz + 1] : 1.0;
+                const double kx = q.k[0][dx + 1], ky = q.k[1][dy + 1], kz = g.d == 3 ? q.k[2][dz + 1] : 0.0;
+                double kc = kx * my * mz + mx * ky * mz;
+                if (g.d == 3) kc += mx * my * kz;
+                int qi = (dx + 1) + 3 * (dy + 1) + (g.d == 3 ? 9 * (dz + 1) : 0);
+                out[(long long)qi * g.nx + p] = mx * my * mz + c * kc;
+            }
+}
+
 // Dense matrix of the coarsest level from its FP64 description (fine or stencil).
 static __global__ void k_dense_level(FineDesc fd, double* Adense) {
     pdl_prologue();
@@ -649,7 +676,8 @@ namespace aao {
 // that travels through HBM).
 // ---------------------------------------------------------------------------
 constexpr int kTailPmax = 4;    // points per thread at level lc (kTailMaxPoints / 1024)
-constexpr int kTailMaxPoints = 4096;
+constexpr int kTailMaxPoints = 4096;         // batched V-cycles
+constexpr int kTailMaxPointsSingle = 1024;   // single-item V-cycles (the Schur sweep)
 constexpr long long kFuseMaxPoints = 1 << 20;   // fuse sweeps below this many points per launch
 
 template <class SI> struct TailCtx {
@@ -673,44 +701,36 @@ __device__ __forceinline__ LevelOp<SI> tail_op(const TailCtx<SI>& t, int l, cons
     return op;
 }
 
+// Damped-Jacobi sweeps of tail level l, ping-ponging between its two on-chip x
+// buffers (one barrier per sweep); cur selects the buffer holding x.
 template <class SI>
 __device__ __forceinline__ void tail_smooth(const TailCtx<SI>& t, int l, typename PT<SI>::A* sm, int sweeps,
-                                            bool zero_first) {
+                                            bool zero_first, int& cur) {
     using A = typename PT<SI>::A;
     const LevelOp<SI> op = tail_op(t, l, reinterpret_cast<const unsigned char*>(sm));
     const Geo& g = op.g;
-    A* X = sm + t.off[l];
-    const A* Bv = X + g.nx;
-    View<A> xv{X, nullptr, g.n0};
+    A* X0 = sm + t.off[l];
+    const A* Bv = X0 + 2 * g.nx;
     const int nt = blockDim.x;
     for (int sw = 0; sw < sweeps; ++sw) {
         const bool zero = zero_first && sw == 0;
-        A nv[kTailPmax];
-#pragma unroll
-        for (int i = 0; i < kTailPmax; ++i) {
-            int p = threadIdx.x + i * nt;
-            nv[i] = A(0);
-            if (p < g.nx) {
-                int c = p % g.n0;
-                long long row = p / g.n0;
-                int j = (int)(row % g.n1), k = (int)(row / g.n1);
+        const A* Xc = X0 + (long long)cur * g.nx;
+        A* Xn = X0 + (long long)(1 - cur) * g.nx;
+        View<A> xv{Xc, nullptr, g.n0};
+        for (int p = threadIdx.x; p < g.nx; p += nt) {
+            int c = p % g.n0;
+            long long row = p / g.n0;
+            int j, k;
+    row_jk(g, row, j, k);
+            if (zero) {
+                Xn[p] = t.omega * Bv[p] / level_diag(op, row, j, k, c);
+            } else {
                 A Au, dg;
-                if (zero) {
-                    if (op.fine) dg = op.sigma + op.c * fd_K_diag<A>(g, op.faces, row, j, k, c);
-                    else dg = sten_coef(op, g.d == 3 ? 13 : 4, p);
-                    nv[i] = t.omega * Bv[p] / dg;
-                } else {
-                    level_apply(op, xv, row, j, k, c, Au, dg);
-                    nv[i] = X[p] + t.omega * (Bv[p] - Au) / dg;
-                }
+                level_apply(op, xv, row, j, k, c, Au, dg);
+                Xn[p] = Xc[p] + t.omega * (Bv[p] - Au) / dg;
             }
         }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < kTailPmax; ++i) {
-            int p = threadIdx.x + i * nt;
-            if (p < g.nx) X[p] = nv[i];
-        }
+        cur = 1 - cur;
         __syncthreads();
     }
 }
@@ -726,6 +746,9 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
     if (b >= B || (active && !active[b])) return;
     const int nt = blockDim.x, tid = threadIdx.x;
     const int lc = t.lc, L = t.L;
+    // per level: X0, X1 (x ping-pong; the free one holds the residual), B
+    int cur[kMaxLevels];
+    for (int l = 0; l < kMaxLevels; ++l) cur[l] = 0;
     // copy the coarse stencils of levels >= stage_from into shared memory
     for (int l = t.stage_from; l < L; ++l) {
         if (l < 1) continue;
@@ -736,7 +759,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
     {
         const Geo& g = t.op[lc].g;
         A* X = sm + t.off[lc];
-        A* Bv = X + g.nx;
+        A* Bv = X + 2 * g.nx;
         View<SI> bs = view_of(bv, b, 0, g.n0);
         const bool has = xin.d != nullptr;
         View<SI> xs = has ? view_of(xin, b, 0, g.n0) : View<SI>{nullptr, nullptr, g.n0};
@@ -752,24 +775,25 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
         const LevelOp<SI> op = tail_op(t, l, tail_smem);
         const Geo& gf = op.g;
         const Geo& gc = t.op[l + 1].g;
-        A* X = sm + t.off[l];
-        A* Bv = X + gf.nx;
         if (t.nu1 > 0) {
-            tail_smooth(t, l, sm, t.nu1, xzero);
+            tail_smooth(t, l, sm, t.nu1, xzero, cur[l]);
             xzero = false;
         }
+        A* X0 = sm + t.off[l];
+        const A* Xf = X0 + (long long)cur[l] * gf.nx;
+        A* Rf = X0 + (long long)(1 - cur[l]) * gf.nx;   // the free x buffer holds the residual
+        const A* Bv = X0 + 2 * gf.nx;
         A* Xc = sm + t.off[l + 1];
-        A* Bc = Xc + gc.nx;
-        A* Rf = Bv + gf.nx;
-        // residual of this level once (on chip), then the restriction P^T r
+        A* Bc = Xc + 2 * gc.nx;
         if (xzero) {
             for (int p = tid; p < gf.nx; p += nt) Rf[p] = Bv[p];
         } else {
-            View<A> xv{X, nullptr, gf.n0};
+            View<A> xv{Xf, nullptr, gf.n0};
             for (int p = tid; p < gf.nx; p += nt) {
                 int c = p % gf.n0;
                 long long row = p / gf.n0;
-                int j = (int)(row % gf.n1), k = (int)(row / gf.n1);
+                int j, k;
+    row_jk(gf, row, j, k);
                 A Au, dg;
                 level_apply(op, xv, row, j, k, c, Au, dg);
                 Rf[p] = Bv[p] - Au;
@@ -779,7 +803,8 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
         for (int P = tid; P < gc.nx; P += nt) {
             int I = P % gc.n0;
             long long crow = P / gc.n0;
-            int J = (int)(crow % gc.n1), Kc = (int)(crow / gc.n1);
+            int J, Kc;
+    row_jk(gc, crow, J, Kc);
             A acc = A(0);
             const int zlo = gf.d == 3 ? -1 : 0, zhi = gf.d == 3 ? 1 : 0;
             for (int dz = zlo; dz <= zhi; ++dz) {
@@ -800,19 +825,16 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
                 }
             }
             Bc[P] = acc;
-            Xc[P] = A(0);
+            Xc[P] = A(0);      // coarse levels start from zero (buffer 0)
         }
         __syncthreads();
-        xzero = true;   // coarse levels start from zero
+        xzero = true;
     }
     {
         const Geo& g = t.op[L - 1].g;
-        A* X = sm + t.off[L - 1];
-        const A* Bv = X + g.nx;
+        A* X = sm + t.off[L - 1] + (long long)cur[L - 1] * g.nx;
+        const A* Bv = sm + t.off[L - 1] + 2 * g.nx;
         const int nc = (int)g.nx;
-        if (L - 1 == lc && !xzero) {
-            // a single-level tail with a nonzero guess is still the exact solve
-        }
         for (int p = tid; p < nc; p += nt) {
             A acc = A(0);
             for (int q = 0; q < nc; ++q) acc += t.Dinv[(long long)p * nc + q] * Bv[q];
@@ -823,12 +845,13 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
     for (int l = L - 2; l >= lc; --l) {
         const Geo& gf = t.op[l].g;
         const Geo& gc = t.op[l + 1].g;
-        A* X = sm + t.off[l];
-        const A* Xc = sm + t.off[l + 1];
+        A* X = sm + t.off[l] + (long long)cur[l] * gf.nx;
+        const A* Xc = sm + t.off[l + 1] + (long long)cur[l + 1] * gc.nx;
         for (int p = tid; p < gf.nx; p += nt) {
             int c = p % gf.n0;
             long long row = p / gf.n0;
-            int j = (int)(row % gf.n1), k = (int)(row / gf.n1);
+            int j, k;
+    row_jk(gf, row, j, k);
             int Jx[2], Jy[2], Jz[2] = {0, 0};
             float wx[2], wy[2], wz[2] = {1.f, 0.f};
             int mx = interp_1d(c, gc.n0, Jx, wx);
@@ -842,12 +865,206 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
             X[p] = acc;
         }
         __syncthreads();
-        if (t.nu2 > 0) tail_smooth(t, l, sm, t.nu2, false);
+        if (t.nu2 > 0) tail_smooth(t, l, sm, t.nu2, false, cur[l]);
     }
     // write level lc
     {
         const Geo& g = t.op[lc].g;
-        const A* X = sm + t.off[lc];
+        const A* X = sm + t.off[lc] + (long long)cur[lc] * g.nx;
+        const int w = tid >> 5, lane = tid & 31, nw = nt >> 5;
+        for (long long row = w; row < g.R; row += nw) {
+            SI* o;
+            float* osc;
+            row_store_ptrs(xout, b, 0, row, g.n0, o, osc);
+            row_store<SI>(o, osc, g.n0, lane, [&](int c) -> A { return X[row * g.n0 + c]; });
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2D specialisation of the fused tail: a 32 x 32 thread block maps (column,
+// row) directly, stencils are the unrolled 9-point (stored) or 5-point
+// (matrix-free fine level) forms.  Same levels, buffers and arithmetic as
+// k_vcycle_tail; only the indexing work per point is smaller.
+// ---------------------------------------------------------------------------
+template <class SI>
+__device__ __forceinline__ typename PT<SI>::A tail2d_apply(const LevelOp<SI>& op, const typename PT<SI>::A* X, int c,
+                                                           int j, typename PT<SI>::A& diag) {
+    using A = typename PT<SI>::A;
+    const Geo& g = op.g;
+    const int n0 = g.n0, n1 = g.n1;
+    if (op.fine) {
+        A Au, dg;
+        View<A> xv{X, nullptr, n0};
+        level_apply(op, xv, j, j, 0, c, Au, dg);
+        diag = dg;
+        return Au;
+    }
+    const long long p = (long long)j * n0 + c;
+    A acc = A(0);
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int jj = j + dy;
+        if (jj < 0 || jj >= n1) continue;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int cc = c + dx;
+            if (cc < 0 || cc >= n0) continue;
+            acc += sten_coef(op, (dx + 1) + 3 * (dy + 1), p) * X[jj * n0 + cc];
+        }
+    }
+    diag = sten_coef(op, 4, p);
+    return acc;
+}
+
+template <class SI>
+__device__ __forceinline__ void tail2d_smooth(const TailCtx<SI>& t, int l, typename PT<SI>::A* sm, int sweeps,
+                                              bool zero_first, int& cur) {
+    using A = typename PT<SI>::A;
+    const LevelOp<SI> op = tail_op(t, l, reinterpret_cast<const unsigned char*>(sm));
+    const Geo& g = op.g;
+    A* X0 = sm + t.off[l];
+    const A* Bv = X0 + 2 * g.nx;
+    for (int sw = 0; sw < sweeps; ++sw) {
+        const bool zero = zero_first && sw == 0;
+        const A* Xc = X0 + (long long)cur * g.nx;
+        A* Xn = X0 + (long long)(1 - cur) * g.nx;
+        for (int j = threadIdx.y; j < g.n1; j += blockDim.y)
+            for (int c = threadIdx.x; c < g.n0; c += blockDim.x) {
+                const int p = j * g.n0 + c;
+                if (zero) {
+                    Xn[p] = t.omega * Bv[p] / level_diag(op, j, j, 0, c);
+                } else {
+                    A dg;
+                    const A Au = tail2d_apply(op, Xc, c, j, dg);
+                    Xn[p] = Xc[p] + t.omega * (Bv[p] - Au) / dg;
+                }
+            }
+        cur = 1 - cur;
+        __syncthreads();
+    }
+}
+
+template <class SI>
+__global__ void __launch_bounds__(1024) k_vcycle_tail_2d(TailCtx<SI> t, int B, const int* active, Vec<SI> bv,
+                                                         Vec<SI> xin, Vec<SI> xout) {
+    pdl_prologue();
+    using A = typename PT<SI>::A;
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    A* sm = reinterpret_cast<A*>(tail_smem);
+    const int b = blockIdx.x;
+    if (b >= B || (active && !active[b])) return;
+    const int tx = threadIdx.x, ty = threadIdx.y, bx = blockDim.x, by = blockDim.y;
+    const int tid = ty * bx + tx, nt = bx * by;
+    const int lc = t.lc, L = t.L;
+    int cur[kMaxLevels];
+    for (int l = 0; l < kMaxLevels; ++l) cur[l] = 0;
+    for (int l = t.stage_from; l < L; ++l) {
+        if (l < 1) continue;
+        const int n = t.op[l].ncoef * (int)t.op[l].g.nx;
+        SI* dst = reinterpret_cast<SI*>(tail_smem + t.sten_off[l]);
+        for (int i = tid; i < n; i += nt) dst[i] = t.op[l].sten[i];
+    }
+    {
+        const Geo& g = t.op[lc].g;
+        A* X = sm + t.off[lc];
+        A* Bv = X + 2 * g.nx;
+        View<SI> bs = view_of(bv, b, 0, g.n0);
+        const bool has = xin.d != nullptr;
+        View<SI> xs = has ? view_of(xin, b, 0, g.n0) : View<SI>{nullptr, nullptr, g.n0};
+        for (int j = ty; j < g.n1; j += by)
+            for (int c = tx; c < g.n0; c += bx) {
+                const int p = j * g.n0 + c;
+                Bv[p] = bs.at(j, c);
+                X[p] = has ? xs.at(j, c) : A(0);
+            }
+    }
+    __syncthreads();
+    bool xzero = xin.d == nullptr;
+    for (int l = lc; l < L - 1; ++l) {
+        const LevelOp<SI> op = tail_op(t, l, tail_smem);
+        const Geo& gf = op.g;
+        const Geo& gc = t.op[l + 1].g;
+        if (t.nu1 > 0) {
+            tail2d_smooth(t, l, sm, t.nu1, xzero, cur[l]);
+            xzero = false;
+        }
+        A* X0 = sm + t.off[l];
+        const A* Xf = X0 + (long long)cur[l] * gf.nx;
+        A* Rf = X0 + (long long)(1 - cur[l]) * gf.nx;
+        const A* Bv = X0 + 2 * gf.nx;
+        for (int j = ty; j < gf.n1; j += by)
+            for (int c = tx; c < gf.n0; c += bx) {
+                const int p = j * gf.n0 + c;
+                if (xzero) {
+                    Rf[p] = Bv[p];
+                } else {
+                    A dg;
+                    Rf[p] = Bv[p] - tail2d_apply(op, Xf, c, j, dg);
+                }
+            }
+        __syncthreads();
+        A* Xc = sm + t.off[l + 1];
+        A* Bc = Xc + 2 * gc.nx;
+        for (int J = ty; J < gc.n1; J += by)
+            for (int I = tx; I < gc.n0; I += bx) {
+                A acc = A(0);
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int fj = 2 * J + 1 + dy;
+                    if (fj < 0 || fj >= gf.n1) continue;
+                    const A wy = dy == 0 ? A(1) : A(0.5);
+#pragma unroll
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int fi = 2 * I + 1 + dx;
+                        if (fi < 0 || fi >= gf.n0) continue;
+                        const A wx = dx == 0 ? A(1) : A(0.5);
+                        acc += wx * wy * Rf[fj * gf.n0 + fi];
+                    }
+                }
+                Bc[J * gc.n0 + I] = acc;
+                Xc[J * gc.n0 + I] = A(0);
+            }
+        __syncthreads();
+        xzero = true;
+    }
+    {
+        const Geo& g = t.op[L - 1].g;
+        A* X = sm + t.off[L - 1] + (long long)cur[L - 1] * g.nx;
+        const A* Bv = sm + t.off[L - 1] + 2 * g.nx;
+        const int nc = (int)g.nx;
+        for (int p = tid; p < nc; p += nt) {
+            A acc = A(0);
+            for (int q = 0; q < nc; ++q) acc += t.Dinv[(long long)p * nc + q] * Bv[q];
+            X[p] = acc;
+        }
+    }
+    __syncthreads();
+    for (int l = L - 2; l >= lc; --l) {
+        const Geo& gf = t.op[l].g;
+        const Geo& gc = t.op[l + 1].g;
+        A* X = sm + t.off[l] + (long long)cur[l] * gf.nx;
+        const A* Xc = sm + t.off[l + 1] + (long long)cur[l + 1] * gc.nx;
+        for (int j = ty; j < gf.n1; j += by) {
+            int Jy[2];
+            float wy[2];
+            const int my = interp_1d(j, gc.n1, Jy, wy);
+            for (int c = tx; c < gf.n0; c += bx) {
+                int Jx[2];
+                float wx[2];
+                const int mx = interp_1d(c, gc.n0, Jx, wx);
+                A acc = X[j * gf.n0 + c];
+                for (int q = 0; q < my; ++q)
+                    for (int e = 0; e < mx; ++e) acc += A(wy[q]) * A(wx[e]) * Xc[Jy[q] * gc.n0 + Jx[e]];
+                X[j * gf.n0 + c] = acc;
+            }
+        }
+        __syncthreads();
+        if (t.nu2 > 0) tail2d_smooth(t, l, sm, t.nu2, false, cur[l]);
+    }
+    {
+        const Geo& g = t.op[lc].g;
+        const A* X = sm + t.off[lc] + (long long)cur[lc] * g.nx;
         const int w = tid >> 5, lane = tid & 31, nw = nt >> 5;
         for (long long row = w; row < g.R; row += nw) {
             SI* o;

@@ -199,7 +199,7 @@ extern "C" aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double 
             const Geo& gl = lev[l];
             const PtMap pm = ptmap(gl.n0);
             if (l == L - 1) {
-                launch(k_coarse_solve<double>, pt_blocks(pm, gl.R), pt_threads(pm), 0, st, gl, pm, 1, (const int*)nullptr, dinv,
+                launch(k_coarse_solve<double>, pt_grid(pm, gl.R, 1), pt_block(pm), 0, st, gl, pm, 1, (const int*)nullptr, dinv,
                        bvec, xout);
                 AAO_LAUNCH_CHECK();
                 return AAO_OK;
@@ -216,18 +216,18 @@ extern "C" aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double 
             };
             for (int q = 0; q < pre; ++q) {
                 Vec<double> d = dest();
-                launch(k_smooth<double>, pt_blocks(pm, gl.R), pt_threads(pm), 0, st, op, pm, 1, (const int*)nullptr, cur,
+                launch(k_smooth<double>, pt_grid(pm, gl.R, 1), pt_block(pm), 0, st, op, pm, 1, (const int*)nullptr, cur,
                        bvec, d, omega);
                 cur = d;
             }
             const Geo& gc = lev[l + 1];
             if (cur.d == nullptr) {
-                launch(k_restrict<double>, pt_blocks(pmc, gc.R), pt_threads(pmc), 0, st, gl, gc, pmc, 1, (const int*)nullptr, bvec,
+                launch(k_restrict<double>, pt_grid(pmc, gc.R, 1), pt_block(pmc), 0, st, gl, gc, pmc, 1, (const int*)nullptr, bvec,
                        Bb[l + 1]);
             } else {
-                launch(k_residual<double>, pt_blocks(pm, gl.R), pt_threads(pm), 0, st, op, pm, 1, (const int*)nullptr, cur, bvec,
+                launch(k_residual<double>, pt_grid(pm, gl.R, 1), pt_block(pm), 0, st, op, pm, 1, (const int*)nullptr, cur, bvec,
                        Rr[l]);
-                launch(k_restrict<double>, pt_blocks(pmc, gc.R), pt_threads(pmc), 0, st, gl, gc, pmc, 1, (const int*)nullptr,
+                launch(k_restrict<double>, pt_grid(pmc, gc.R, 1), pt_block(pmc), 0, st, gl, gc, pmc, 1, (const int*)nullptr,
                        Rr[l], Bb[l + 1]);
             }
             AAO_LAUNCH_CHECK();
@@ -235,13 +235,13 @@ extern "C" aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double 
                         st, ops));
             {
                 Vec<double> d = dest();
-                launch(k_prolong_add<double>, pt_blocks(pm, gl.R), pt_threads(pm), 0, st, gl, gc, pm, 1, (const int*)nullptr,
+                launch(k_prolong_add<double>, pt_grid(pm, gl.R, 1), pt_block(pm), 0, st, gl, gc, pm, 1, (const int*)nullptr,
                        X[l + 1], cur, d);
                 cur = d;
             }
             for (int q = 0; q < post; ++q) {
                 Vec<double> d = dest();
-                launch(k_smooth<double>, pt_blocks(pm, gl.R), pt_threads(pm), 0, st, op, pm, 1, (const int*)nullptr, cur,
+                launch(k_smooth<double>, pt_grid(pm, gl.R, 1), pt_block(pm), 0, st, op, pm, 1, (const int*)nullptr, cur,
                        bvec, d, omega);
                 cur = d;
             }

@@ -41,6 +41,8 @@ class Precond : public PrecondBase {
     Level lev[kMaxLevels];
     A* Dinv[kMaxS] = {};           // dense coarsest inverse per stage
     Faces<A> facesA;
+    SpaceOp<A> sopA;                 // fine-grid K (and M for Q1) for the stage kernels
+    A* cheb[3] = {};                 // Q1: Chebyshev x, r, d ((nt+1)*nx each)
     int kin = 0;                   // inner maxit
     double itol = 0.0;
     // inner GMRES state
@@ -61,10 +63,16 @@ class Precond : public PrecondBase {
     double* tmp64 = nullptr;       // Bmax*s*nx staging for component entry points
     cudaEvent_t e0, e1, e2;
     int nact = 0;                  // active items of the current batch (exact only while profiling)
-    int lc = 0;                    // first level handled by the fused on-chip tail kernel
+    // Fused on-chip tail: two variants, for single-item V-cycles (the Schur
+    // sweep, where a smaller tail plus fused level kernels is faster) and for
+    // batched V-cycles (every item's tail on its own SM).
+    struct Tail {
+        int lc = 0;                // first level handled by the tail kernel
+        size_t smem = 0;
+        TailCtx<SI> ctx[kMaxS];
+    };
+    Tail tails[2];                 // [0]: B == 1, [1]: B > 1
     int tail_threads = 1024;
-    size_t tail_smem = 0;
-    TailCtx<SI> tctx[kMaxS];
     int* hact = nullptr;           // pinned mirror of activeh (profiling)
 
     cudaStream_t cur_stream = nullptr;     // stream of the next launch (capture stream while capturing)
@@ -159,8 +167,19 @@ class Precond : public PrecondBase {
             facesA.fy = fy;
             facesA.fz = fz;
         }
+        sopA.faces = facesA;
+        sopA.q1 = h->q1;
+        if (h->q1) {
+            for (int a = 0; a < 3; ++a)
+                for (int e = 0; e < 3; ++e) {
+                    sopA.q.m[a][e] = (A)h->q1d.m[a][e];
+                    sopA.q.k[a][e] = (A)h->q1d.k[a][e];
+                }
+        }
         // ---- Galerkin hierarchy per stage shift c_i = tau d_i
         const int ncoef = g0.d == 3 ? 27 : 9;
+        double* sten0 = nullptr;             // Q1: stored fine-level stencil of M + c K (FP64)
+        if (h->q1) AAO_TRY(ar.alloc(&sten0, (size_t)(ncoef * g0.nx)));
         double* sten64[kMaxLevels] = {};
         for (int l = 1; l < L; ++l) AAO_TRY(ar.alloc(&sten64[l], (size_t)(ncoef * lev[l].g.nx)));
         const Geo& gcst = lev[L - 1].g;
@@ -179,33 +198,20 @@ class Precond : public PrecondBase {
             fd.c = h->tau * h->D[i];
             fd.faces = h->faces64;
             fd.sten = nullptr;
+            if (h->q1) {
+                launch(k_q1_stencil, (unsigned)((g0.nx + 127) / 128), 128, 0, st(), g0, h->q1d, h->tau * h->D[i],
+                       sten0);
+                AAO_LAUNCH_CHECK();
+                AAO_TRY(store_stencil(0, i, sten0, ncoef));
+                fd.fine = 0;
+                fd.sigma = 0.0;
+                fd.c = 0.0;
+                fd.sten = sten0;
+            }
             for (int l = 1; l < L; ++l) {
                 launch(k_galerkin, (unsigned)((lev[l].g.nx + 127) / 128), 128, 0, st(), fd, lev[l].g, sten64[l]);
                 AAO_LAUNCH_CHECK();
-                // store in SI
-                if constexpr (std::is_same<SI, double>::value) {
-                    SI* keep;
-                    AAO_TRY(ar.alloc(&keep, (size_t)(ncoef * lev[l].g.nx)));
-                    AAO_CUDA_TRY(cudaMemcpyAsync(keep, sten64[l], sizeof(double) * ncoef * lev[l].g.nx,
-                                                 cudaMemcpyDeviceToDevice, st()));
-                    lev[l].sten[i] = keep;
-                } else {
-                    float* sc;
-                    AAO_TRY(ar.alloc(&sc, ncoef));
-                    if (PT<SI>::scaled) {
-                        launch(k_stencil_absmax, ncoef, kBlock, 0, st(), sten64[l], lev[l].g.nx, sc);
-                    } else {
-                        AAO_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(float) * ncoef, st()));
-                    }
-                    SI* out;
-                    AAO_TRY(ar.alloc(&out, (size_t)(ncoef * lev[l].g.nx)));
-                    long long tot = ncoef * lev[l].g.nx;
-                    launch(k_stencil_convert<SI>, (unsigned)((tot + 255) / 256), 256, 0, st(), 
-                        sten64[l], lev[l].g.nx, ncoef, sc, out);
-                    AAO_LAUNCH_CHECK();
-                    lev[l].sten[i] = out;
-                    lev[l].sten_sc[i] = sc;
-                }
+                AAO_TRY(store_stencil(l, i, sten64[l], ncoef));
                 FineDesc nd;
                 nd.g = lev[l].g;
                 nd.fine = 0;
@@ -218,11 +224,11 @@ class Precond : public PrecondBase {
             FineDesc cd;
             if (L == 1) {
                 cd.g = g0;
-                cd.fine = 1;
-                cd.sigma = 1.0;
-                cd.c = h->tau * h->D[i];
+                cd.fine = h->q1 ? 0 : 1;
+                cd.sigma = h->q1 ? 0.0 : 1.0;
+                cd.c = h->q1 ? 0.0 : h->tau * h->D[i];
                 cd.faces = h->faces64;
-                cd.sten = nullptr;
+                cd.sten = h->q1 ? sten0 : nullptr;
             } else {
                 cd.g = gcst;
                 cd.fine = 0;
@@ -245,66 +251,18 @@ class Precond : public PrecondBase {
             set_error("coarsest multigrid operator is not positive definite");
             return AAO_ERR_BREAKDOWN;
         }
-        // ---- fused tail: the coarsest levels that fit on one SM
+        // ---- fused tails: the coarsest levels that fit on one SM
+        int optin = 0;
         {
-            const size_t cap = 200 * 1024;
-            const int ncf = g0.d == 3 ? 27 : 9;
-            lc = L - 1;
-            size_t acc = 0;
-            for (int l = L - 1; l >= 0; --l) {
-                acc += 3 * (size_t)lev[l].g.nx * sizeof(A);
-                // the tail runs on one SM: its top level stays small
-                if (lev[l].g.nx > kTailMaxPoints || lev[l].g.nx > (long long)kTailPmax * tail_threads || acc > cap)
-                    break;
-                lc = l;
-            }
-            size_t vec_bytes = 0;
-            for (int l = lc; l < L; ++l) vec_bytes += 3 * (size_t)lev[l].g.nx * sizeof(A);
-            vec_bytes = (vec_bytes + 15) / 16 * 16;
-            // stage as many of the coarsest stencils as fit next to the vectors
-            int stage_from = L;
-            size_t sb = 0;
-            for (int l = L - 1; l >= (lc > 1 ? lc : 1); --l) {
-                size_t add = ((size_t)ncf * lev[l].g.nx * sizeof(SI) + 15) / 16 * 16;
-                if (vec_bytes + sb + add > cap) break;
-                sb += add;
-                stage_from = l;
-            }
-            tail_smem = vec_bytes + sb;
-            for (int i = 0; i < s; ++i) {
-                TailCtx<SI>& t = tctx[i];
-                t.lc = lc;
-                t.L = L;
-                int o = 0;
-                for (int l = lc; l < L; ++l) {
-                    t.op[l] = level_op(l, i);
-                    t.off[l] = o;
-                    o += 3 * (int)lev[l].g.nx;
-                }
-                t.vec_bytes = (int)vec_bytes;
-                t.stage_from = stage_from;
-                size_t so = vec_bytes;
-                for (int l = 0; l < kMaxLevels; ++l) t.sten_off[l] = 0;
-                for (int l = stage_from; l < L; ++l) {
-                    t.sten_off[l] = (int)so;
-                    so += ((size_t)ncf * lev[l].g.nx * sizeof(SI) + 15) / 16 * 16;
-                }
-                t.Dinv = Dinv[i];
-                t.omega = (A)h->opt.mg_omega;
-                t.nu1 = h->opt.mg_pre;
-                t.nu2 = h->opt.mg_post;
-            }
-            // the attribute is per kernel for the whole process: always set the device's
-            // opt-in maximum so that handles with larger tails keep working
-            int dev = 0, optin = 0;
+            int dev = 0;
             AAO_CUDA_TRY(cudaGetDevice(&dev));
             AAO_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-            if ((int)tail_smem > optin) {
-                set_error("fused multigrid tail does not fit in shared memory");
-                return AAO_ERR_ARG;
-            }
-            AAO_CUDA_TRY(cudaFuncSetAttribute(k_vcycle_tail<SI>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         }
+        for (int v = 0; v < 2; ++v) AAO_TRY(build_tail(tails[v], v == 0 ? kTailMaxPointsSingle : kTailMaxPoints, optin));
+        // the attribute is per kernel for the whole process: always set the device's
+        // opt-in maximum so that handles with larger tails keep working
+        AAO_CUDA_TRY(cudaFuncSetAttribute(k_vcycle_tail<SI>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        AAO_CUDA_TRY(cudaFuncSetAttribute(k_vcycle_tail_2d<SI>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         // ---- level scratch
         for (int l = 0; l < L; ++l) {
             const Geo& gl = lev[l].g;
@@ -346,6 +304,8 @@ class Precond : public PrecondBase {
         AAO_TRY(ar.alloc(&tV, (size_t)(h->nt * item)));
         AAO_TRY(ar.alloc(&tmp64, (size_t)(Bmax * item)));
         AAO_TRY(ar.alloc(&stepp, 1));
+        if (h->q1)
+            for (int i = 0; i < 3; ++i) AAO_TRY(ar.alloc(&cheb[i], (size_t)((h->nt + 1) * g0.nx)));
         AAO_CUDA_TRY(cudaEventCreate(&e0));
         AAO_CUDA_TRY(cudaEventCreate(&e1));
         AAO_CUDA_TRY(cudaEventCreate(&e2));
@@ -354,12 +314,123 @@ class Precond : public PrecondBase {
         return AAO_OK;
     }
 
+    // Choose the tail's top level (at most max_points points, shared memory within the
+    // device limit) and fill its per-stage contexts.
+    aao_status build_tail(Tail& T, long long max_points, int optin) {
+        const Geo& g0 = h->g;
+        const int s = h->s;
+        const size_t cap = 200 * 1024;
+        const int ncf = g0.d == 3 ? 27 : 9;
+        int lc = L - 1;
+        size_t acc = 0;
+        for (int l = L - 1; l >= 0; --l) {
+            acc += 3 * (size_t)lev[l].g.nx * sizeof(A);
+            if (lev[l].g.nx > max_points || lev[l].g.nx > (long long)kTailPmax * tail_threads || acc > cap) break;
+            lc = l;
+        }
+        size_t vec_bytes = 0;
+        for (int l = lc; l < L; ++l) vec_bytes += 3 * (size_t)lev[l].g.nx * sizeof(A);
+        vec_bytes = (vec_bytes + 15) / 16 * 16;
+        // stage as many of the coarsest stencils as fit next to the vectors
+        int stage_from = L;
+        size_t sb = 0;
+        for (int l = L - 1; l >= (lc > 1 ? lc : 1); --l) {
+            size_t add = ((size_t)ncf * lev[l].g.nx * sizeof(SI) + 15) / 16 * 16;
+            if (vec_bytes + sb + add > cap) break;
+            sb += add;
+            stage_from = l;
+        }
+        T.lc = lc;
+        T.smem = vec_bytes + sb;
+        if ((long long)T.smem > optin) {
+            set_error("fused multigrid tail does not fit in shared memory");
+            return AAO_ERR_ARG;
+        }
+        for (int i = 0; i < s; ++i) {
+            TailCtx<SI>& t = T.ctx[i];
+            t.lc = lc;
+            t.L = L;
+            int o = 0;
+            for (int l = lc; l < L; ++l) {
+                t.op[l] = level_op(l, i);
+                t.off[l] = o;
+                o += 3 * (int)lev[l].g.nx;
+            }
+            t.vec_bytes = (int)vec_bytes;
+            t.stage_from = stage_from;
+            size_t so = vec_bytes;
+            for (int l = 0; l < kMaxLevels; ++l) t.sten_off[l] = 0;
+            for (int l = stage_from; l < L; ++l) {
+                t.sten_off[l] = (int)so;
+                so += ((size_t)ncf * lev[l].g.nx * sizeof(SI) + 15) / 16 * 16;
+            }
+            t.Dinv = Dinv[i];
+            t.omega = (A)h->opt.mg_omega;
+            t.nu1 = h->opt.mg_pre;
+            t.nu2 = h->opt.mg_post;
+        }
+        return AAO_OK;
+    }
+
+    // Keep the FP64 stencil of level l (shift `stage`) in the P_int storage type.
+    aao_status store_stencil(int l, int i, const double* s64, int ncoef) {
+        const long long n = (long long)ncoef * lev[l].g.nx;
+        if constexpr (std::is_same<SI, double>::value) {
+            SI* keep;
+            AAO_TRY(ar.alloc(&keep, (size_t)n));
+            AAO_CUDA_TRY(cudaMemcpyAsync(keep, s64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st()));
+            lev[l].sten[i] = keep;
+        } else {
+            float* sc;
+            AAO_TRY(ar.alloc(&sc, ncoef));
+            if (PT<SI>::scaled) {
+                launch(k_stencil_absmax, ncoef, kBlock, 0, st(), s64, lev[l].g.nx, sc);
+            } else {
+                AAO_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(float) * ncoef, st()));
+            }
+            SI* out;
+            AAO_TRY(ar.alloc(&out, (size_t)n));
+            launch(k_stencil_convert<SI>, (unsigned)((n + 255) / 256), 256, 0, st(), s64, lev[l].g.nx, ncoef,
+                   (const float*)sc, out);
+            AAO_LAUNCH_CHECK();
+            lev[l].sten[i] = out;
+            lev[l].sten_sc[i] = sc;
+        }
+        return AAO_OK;
+    }
+
+    // Q1: buf <- M^{-1} buf for B blocks of n_x by `cheb_steps` Chebyshev steps
+    // with Jacobi splitting on the spectrum bounds [2^-d, (3/2)^d] of D^{-1}M.
+    aao_status mass_inverse(A* buf, int B) {
+        const Geo& g = h->g;
+        const long long n = (long long)B * g.nx;
+        const double lo = std::pow(0.5, g.d), hi = std::pow(1.5, g.d);
+        const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+        double dinv = 1.0;
+        for (int a = 0; a < g.d; ++a) dinv /= h->q1d.m[a][1];
+        double rho = 1.0 / sigma;
+        const unsigned nb = (unsigned)((n + 255) / 256);
+        const PtMap pm = ptmap(g.n0);
+        launch(k_cheb_init<A>, nb, 256, 0, st(), n, (const A*)buf, (A)(dinv / theta), cheb[0], cheb[1], cheb[2]);
+        for (int it = 0; it < h->opt.cheb_steps; ++it) {
+            launch(k_cheb_a<A>, pt_grid(pm, g.R, B), pt_block(pm), 0, st(), g, pm, B, sopA.q,
+                   (const A*)cheb[2], cheb[0], cheb[1]);
+            const double rn = 1.0 / (2.0 * sigma - rho);
+            launch(k_cheb_b<A>, nb, 256, 0, st(), n, (A)(rn * rho), (A)(2.0 * rn / delta * dinv), (const A*)cheb[1],
+                   cheb[2]);
+            rho = rn;
+        }
+        AAO_CUDA_TRY(cudaMemcpyAsync(buf, cheb[0], sizeof(A) * n, cudaMemcpyDeviceToDevice, st()));
+        AAO_LAUNCH_CHECK();
+        return AAO_OK;
+    }
+
     // ---------------------------------------------------------------- MG
     LevelOp<SI> level_op(int l, int stage) const {
         LevelOp<SI> op;
         op.g = lev[l].g;
         op.ncoef = op.g.d == 3 ? 27 : 9;
-        if (l == 0) {
+        if (l == 0 && !h->q1) {
             op.fine = 1;
             op.sigma = A(1);
             op.c = (A)(h->tau * h->D[stage]);
@@ -382,16 +453,21 @@ class Precond : public PrecondBase {
     aao_status vcycle(int l, int stage, int B, const int* act, Vec<SI> xin, Vec<SI> b, Vec<SI> xout) {
         const Geo& g = lev[l].g;
         const PtMap pm = ptmap(g.n0);
-        const unsigned pbl = pt_blocks(pm, (long long)B * g.R), pth = pt_threads(pm);
-        if (l == lc) {
+        const dim3 pbl = pt_grid(pm, g.R, B), pth = pt_block(pm);
+        const Tail& T = tails[B > 1 ? 1 : 0];
+        if (l == T.lc) {
             bytes_hint((xin.d ? 3.0 : 2.0) * nact * g.nx * sizeof(SI));
-            launch(k_vcycle_tail<SI>, (unsigned)B, tail_threads, tail_smem, st(), tctx[stage], B, act, b, xin, xout);
+            if (g.d == 2)
+                launch(k_vcycle_tail_2d<SI>, (unsigned)B, dim3(32, 32), T.smem, st(), T.ctx[stage], B, act, b, xin,
+                       xout);
+            else
+                launch(k_vcycle_tail<SI>, (unsigned)B, tail_threads, T.smem, st(), T.ctx[stage], B, act, b, xin, xout);
             AAO_LAUNCH_CHECK();
             return AAO_OK;
         }
         if (l == L - 1) {
             bytes_hint(2.0 * nact * g.nx * sizeof(SI));
-            launch(k_coarse_solve<SI>, pt_blocks(pm, (long long)B * g.R), pt_threads(pm), 0, st(), g, pm, B, act, Dinv[stage], b,
+            launch(k_coarse_solve<SI>, pt_grid(pm, g.R, B), pt_block(pm), 0, st(), g, pm, B, act, Dinv[stage], b,
                    xout);
             AAO_LAUNCH_CHECK();
             return AAO_OK;
@@ -399,7 +475,7 @@ class Precond : public PrecondBase {
         LevelOp<SI> op = level_op(l, stage);
         const Geo& gc = lev[l + 1].g;
         const PtMap pmc = ptmap(gc.n0);
-        const unsigned cbl = pt_blocks(pmc, (long long)B * gc.R), cth = pt_threads(pmc);
+        const dim3 cbl = pt_grid(pmc, gc.R, B), cth = pt_block(pmc);
         const A om = (A)h->opt.mg_omega;
         const int nu1 = h->opt.mg_pre, nu2 = h->opt.mg_post;
         // Fused kernels trade recomputation for launches: they pay off where the
@@ -487,8 +563,8 @@ class Precond : public PrecondBase {
             int i = transpose ? s - 1 - t : t;
             const double* coef = (transpose ? h->d_LDb : h->d_LDf) + i * s;
             bytes_hint(1.0 * nact * g.nx * (sizeof(SP) + (transpose ? s - 1 - i : i) * sizeof(SI) + sizeof(SI)));
-            launch(k_rana_rhs<SP, SI>, pt_blocks(pm0, (long long)B * g.R), pt_threads(pm0), 0, st(), g, pm0, B, act, V, i, Z, s,
-                   coef, (A)h->tau, facesA, mgb);
+            launch(k_rana_rhs<SP, SI>, pt_grid(pm0, g.R, B), pt_block(pm0), 0, st(), g, pm0, B, act, V, i, Z, s,
+                   coef, (A)h->tau, sopA, mgb);
             AAO_LAUNCH_CHECK();
             Vec<SI> Zi = shift_vec(Z, (long long)i * g.nx, g.n0);
             AAO_TRY(mg_solve(i, B, act, mgb, Zi));
@@ -507,7 +583,7 @@ class Precond : public PrecondBase {
         const long long item = (long long)s * g.nx;
         const long long rows = (long long)s * g.R;
         const PtMap pm0 = ptmap(g.n0);
-        const unsigned nbp = pt_blocks(pm0, (long long)B * rows), ntp = pt_threads(pm0);
+        const dim3 nbp = pt_grid(pm0, rows, B), ntp = pt_block(pm0);
         Red red = h->red;
         red.nchunk = h->nchunk_for(B, rows * ((g.n0 + kWarp - 1) / kWarp));
         dim3 rgrid(red.nchunk, B);
@@ -522,9 +598,9 @@ class Precond : public PrecondBase {
             Vec<SI> Zk = shift_vec(Z0, k * zstride, g.n0);
             AAO_TRY(rana(B, activeh, Vk, Zk, transpose));
             bytes_hint(1.0 * nact * item * (sizeof(SI) + sizeof(A)));
-            launch(k_theta<SI, A>, pt_blocks(pm0, (long long)B * g.R), pt_threads(pm0), 0, st(), g, pm0, B, (const int*)activeh, Zk,
+            launch(k_theta<SI, A>, pt_grid(pm0, g.R, B), pt_block(pm0), 0, st(), g, pm0, B, (const int*)activeh, Zk,
                    wv, item, s, transpose ? h->d_AT : h->d_A,
-                                                     (A)h->tau, facesA);
+                                                     (A)h->tau, sopA);
             AAO_LAUNCH_CHECK();
             // modified Gram--Schmidt: h_{0,k} = V_0.w; then w -= h_{i-1,k} V_{i-1}, h_{i,k} = V_i.w
             Vec<SP> none{};
@@ -569,7 +645,7 @@ class Precond : public PrecondBase {
         const long long item = (long long)s * g.nx;
         const unsigned nbr = blocks_for_rows(g.R);
         if (!transpose) {
-            launch(k_schur_rhs<A>, nbr, kBlock, 0, st(), g, s, (const StepPtrs*)stepp, tbuf, facesA);
+            launch(k_schur_rhs<A>, nbr, kBlock, 0, st(), g, s, (const StepPtrs*)stepp, tbuf, sopA);
             AAO_TRY(inner<A>(1, tbuf, item, nullptr, 0, 0));
             launch(k_schur_update<SI, A>, nbr, kBlock, 0, st(), g, s, (const A*)wbuf, (const StepPtrs*)stepp, Z0,
                    zstride, (const double*)yh, kin, (const int*)itsh, (const double*)h->d_b, h->tau);
@@ -579,11 +655,11 @@ class Precond : public PrecondBase {
                    (const double*)h->d_b, tbuf);
             AAO_TRY(inner<A>(1, tbuf, item, nullptr, 0, 1));
             Vec<SI> Zc = Z0;
-            launch(k_combine<SI, A>, pt_blocks(ptmap(g.n0), (long long)s * g.R), pt_threads(ptmap(g.n0)), 0, st(), ptmap(g.n0),
+            launch(k_combine<SI, A>, pt_grid(ptmap(g.n0), (long long)s * g.R, 1), pt_block(ptmap(g.n0)), 0, st(), ptmap(g.n0),
                    s * g.R, 1,
                    Zc, zstride, (const double*)yh, kin, (const int*)itsh, qbuf, item, 0);
             launch(k_schurT_update<A>, nbr, kBlock, 0, st(), g, s, (const StepPtrs*)stepp, (const A*)qbuf, h->tau,
-                   facesA);
+                   sopA);
             launch(k_step_add, 1, 1, 0, st(), stepp, -1);
         }
         AAO_LAUNCH_CHECK();
@@ -649,8 +725,17 @@ class Precond : public PrecondBase {
             AAO_TRY(inner<double>(nt, r + nv, item, z + nv, item, 0));
             cudaEventRecord(e1, st());
             long long tot = (nt + 1) * nx;
-            launch(k_schur_g<A>, (unsigned)((tot + 255) / 256), 256, 0, st(), nx, nt, s, r, (const double*)(z + nv),
-                   (const double*)h->d_b, h->tau, wbuf, z);
+            if (h->q1) {
+                // g = r_v - Psi_1 z_V with M, then w = M^{-1} g, z_{v,0} = w_0
+                const PtMap pm = ptmap(g.n0);
+                launch(k_schur_g_q1<A>, pt_grid(pm, g.R, nt + 1), pt_block(pm), 0, st(), g, pm, nt,
+                       s, r, (const double*)(z + nv), (const double*)h->d_b, h->tau, sopA.q, wbuf);
+                AAO_TRY(mass_inverse(wbuf, nt + 1));
+                launch(k_convert<A, double>, (unsigned)((nx + 255) / 256), 256, 0, st(), (const A*)wbuf, z, nx);
+            } else {
+                launch(k_schur_g<A>, (unsigned)((tot + 255) / 256), 256, 0, st(), nx, nt, s, r,
+                       (const double*)(z + nv), (const double*)h->d_b, h->tau, wbuf, z);
+            }
             launch(k_step_set, 1, 1, 0, st(), stepp, z, r, 0);
             AAO_LAUNCH_CHECK();
             AAO_TRY(schur_sweep(0));
@@ -664,8 +749,19 @@ class Precond : public PrecondBase {
             AAO_TRY(schur_sweep(1));
             cudaEventRecord(e1, st());
             long long tot = (long long)nt * item;
-            launch(k_schurT_vrhs<A>, (unsigned)((tot + 255) / 256), 256, 0, st(), nx, nt, s, r + nv, (const double*)z,
-                   (const double*)h->d_b, h->tau, tV);
+            if (h->q1) {
+                // z_v = M^{-1} u (Chebyshev in the recurrence precision), then the stage rhs with M
+                const long long nvx = (long long)(nt + 1) * nx;
+                launch(k_convert<double, A>, (unsigned)((nvx + 255) / 256), 256, 0, st(), (const double*)z, wbuf, nvx);
+                AAO_TRY(mass_inverse(wbuf, nt + 1));
+                launch(k_convert<A, double>, (unsigned)((nvx + 255) / 256), 256, 0, st(), (const A*)wbuf, z, nvx);
+                const PtMap pm = ptmap(g.n0);
+                launch(k_schurT_vrhs_q1<A>, pt_grid(pm, g.R, nt), pt_block(pm), 0, st(), g, pm, nt, s,
+                       r + nv, (const double*)z, (const double*)h->d_b, h->tau, sopA.q, tV);
+            } else {
+                launch(k_schurT_vrhs<A>, (unsigned)((tot + 255) / 256), 256, 0, st(), nx, nt, s, r + nv,
+                       (const double*)z, (const double*)h->d_b, h->tau, tV);
+            }
             AAO_LAUNCH_CHECK();
             AAO_TRY(inner<A>(nt, tV, item, z + nv, item, 1));
             cudaEventRecord(e2, st());
@@ -686,13 +782,13 @@ class Precond : public PrecondBase {
     aao_status shifted_solve(int stage, const double* b, double* x) override {
         const Geo& g = h->g;
         nact = 1;
-        launch(k_scale_store<SI, double>, pt_blocks(ptmap(g.n0), g.R), pt_threads(ptmap(g.n0)), 0, st(), ptmap(g.n0), g.R, 1,
+        launch(k_scale_store<SI, double>, pt_grid(ptmap(g.n0), g.R, 1), pt_block(ptmap(g.n0)), 0, st(), ptmap(g.n0), g.R, 1,
                (const int*)nullptr, b, g.nx,
                                                                              nullptr, 0, mgb);
         AAO_LAUNCH_CHECK();
         Vec<SI> out = Z0;   // item 0, stage 0 of the first Z basis
         AAO_TRY(mg_solve(stage, 1, nullptr, mgb, out));
-        launch(k_load<SI, double>, pt_blocks(ptmap(g.n0), g.R), pt_threads(ptmap(g.n0)), 0, st(), ptmap(g.n0), g.R, 1, out, x,
+        launch(k_load<SI, double>, pt_grid(ptmap(g.n0), g.R, 1), pt_block(ptmap(g.n0)), 0, st(), ptmap(g.n0), g.R, 1, out, x,
                g.nx);
         AAO_LAUNCH_CHECK();
         return AAO_OK;
@@ -702,12 +798,12 @@ class Precond : public PrecondBase {
         const Geo& g = h->g;
         nact = 1;
         const long long rows = (long long)h->s * g.R;
-        launch(k_scale_store<SP, double>, pt_blocks(ptmap(g.n0), rows), pt_threads(ptmap(g.n0)), 0, st(), ptmap(g.n0),
+        launch(k_scale_store<SP, double>, pt_grid(ptmap(g.n0), rows, 1), pt_block(ptmap(g.n0)), 0, st(), ptmap(g.n0),
                (int)rows, 1, (const int*)nullptr, r,
                                                                               (long long)h->s * g.nx, nullptr, 0, V0);
         AAO_LAUNCH_CHECK();
         AAO_TRY(rana(1, nullptr, V0, Z0, transpose));
-        launch(k_load<SI, double>, pt_blocks(ptmap(g.n0), rows), pt_threads(ptmap(g.n0)), 0, st(), ptmap(g.n0), (int)rows, 1,
+        launch(k_load<SI, double>, pt_grid(ptmap(g.n0), rows, 1), pt_block(ptmap(g.n0)), 0, st(), ptmap(g.n0), (int)rows, 1,
                Z0, y, (long long)h->s * g.nx);
         AAO_LAUNCH_CHECK();
         return AAO_OK;

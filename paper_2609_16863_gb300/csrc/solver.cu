@@ -82,7 +82,8 @@ __global__ void k_faces(Geo g, const double* kap, double* fx, double* fy, double
     if (i < nfx) {
         long long row = i / (g.n0 + 1);
         int c = (int)(i % (g.n0 + 1));
-        int j = (int)(row % g.n1), k = (int)(row / g.n1);
+        int j, k;
+    row_jk(g, row, j, k);
         fx[i] = 0.5 * (node(c, j + 1, k + kofs) + node(c + 1, j + 1, k + kofs)) * g.hx2;
         return;
     }
@@ -98,7 +99,8 @@ __global__ void k_faces(Geo g, const double* kap, double* fx, double* fy, double
     if (i < nfz) {
         int c = (int)(i % g.n0);
         long long t = i / g.n0;
-        int j = (int)(t % g.n1), kp = (int)(t / g.n1);
+        int j, kp;
+    row_jk(g, t, j, kp);
         fz[i] = 0.5 * (node(c + 1, j + 1, kp) + node(c + 1, j + 1, kp + 1)) * g.hz2;
     }
 }
@@ -106,7 +108,7 @@ __global__ void k_faces(Geo g, const double* kap, double* fx, double* fy, double
 // grad_kappa_m = -sum_{n,i} sum_{faces f containing node m} 1/2 h^-2 (l_P - l_Q)(W_P - W_Q),
 // W_{n,i} = v_n + tau sum_j a_ij V_{n,j}; one thread per node of the full grid.
 __global__ void k_grad_kappa(Geo g, int nt, Tab tab, double tau, const double* lam, const double* x,
-                             double* grad) {
+                             double* grad, int accumulate) {
     pdl_prologue();
     const long long N0 = g.n0 + 2, N1 = g.n1 + 2, N2 = g.d == 3 ? g.n2 + 2 : 1;
     long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -150,7 +152,7 @@ __global__ void k_grad_kappa(Geo g, int nt, Tab tab, double tau, const double* l
             }
         }
     }
-    grad[m] = -acc;
+    grad[m] = accumulate ? grad[m] - acc : -acc;
 }
 
 __global__ void k_outer_init(double* g, int m, const double* beta, int* flags) {
@@ -205,9 +207,13 @@ static aao_status validate(const aao_grid* grid, double tau, int nt, const aao_t
             set_error("grid sizes and lengths must be positive");
             return AAO_ERR_ARG;
         }
-    if (grid->disc != AAO_DISC_FD) {
-        set_error("only the finite-difference discretisation is built (Q1 is not)");
-        return AAO_ERR_UNSUPPORTED;
+    if (grid->disc != AAO_DISC_FD && grid->disc != AAO_DISC_Q1) {
+        set_error("unknown discretisation");
+        return AAO_ERR_ARG;
+    }
+    if (grid->disc == AAO_DISC_Q1 && grid->kappa) {
+        set_error("variable kappa is defined for the finite-difference discretisation only");
+        return AAO_ERR_ARG;
     }
     if (!(tau > 0.0) || nt < 1) {
         set_error("tau must be > 0 and nt >= 1");
@@ -281,6 +287,8 @@ static aao_status setup_handle(Handle* h, const aao_grid* grid, double tau, int 
     g.hx2 = 1.0 / (hx * hx);
     g.hy2 = 1.0 / (hy * hy);
     g.hz2 = g.d == 3 ? 1.0 / (hz * hz) : 0.0;
+    h->q1 = grid->disc == AAO_DISC_Q1;
+    h->q1d = make_q1<double>(g, hx, hy, hz);
     h->nt = nt;
     h->s = tab->s;
     h->tau = tau;
@@ -298,6 +306,10 @@ static aao_status setup_handle(Handle* h, const aao_grid* grid, double tau, int 
     h->nx = g.nx;
     h->nv = (long long)(nt + 1) * g.nx;
     h->nst = h->nv + (long long)nt * h->s * g.nx;
+    if (h->nst / g.n0 * ((g.n0 + kWarp - 1) / kWarp) >= (1LL << 32)) {
+        set_error("problem too large for the reduction indexing");
+        return AAO_ERR_ARG;
+    }
     const int s = h->s;
     cudaStream_t st = h->stream;
     Arena& ar = h->arena;
@@ -378,9 +390,28 @@ static aao_status setup_handle(Handle* h, const aao_grid* grid, double tau, int 
 // ---------------------------------------------------------------------------
 static aao_status matvec_dev(Handle* h, const double* x, double* y, const double* rhs, int transpose) {
     const Geo& g = h->g;
+    if (h->q1) {
+        bytes_hint(8.0 * h->nst * (rhs ? 3 : 2));
+        launch(k_matvec_q1, blocks_for_rows((long long)(h->nt + 1) * g.R), kBlock, 0, h->stream, g, h->nt, h->tab,
+               h->tau, h->q1d, x, y, rhs, transpose);
+        AAO_LAUNCH_CHECK();
+        return AAO_OK;
+    }
     bytes_hint(8.0 * h->nst * (rhs ? 3 : 2));
     launch(k_matvec, blocks_for_rows((long long)(h->nt + 1) * g.R), kBlock, 0, h->stream, 
         g, h->nt, h->tab, h->tau, h->faces64, x, y, rhs, transpose);
+    AAO_LAUNCH_CHECK();
+    return AAO_OK;
+}
+
+static aao_status rhs_dev(Handle* h, const double* f, int f_time_dep, const double* u0, double* out) {
+    if (h->q1) {
+        const PtMap pm = ptmap(h->g.n0);
+        launch(k_rhs_q1, pt_grid(pm, h->g.R, h->nt * h->s + 2), pt_block(pm), 0, h->stream, h->g, pm,
+               h->nt, h->s, f, f_time_dep, u0, h->q1d, out);
+    } else {
+        launch(k_rhs, (unsigned)((h->nst + 255) / 256), 256, 0, h->stream, h->nx, h->nt, h->s, f, f_time_dep, u0, out);
+    }
     AAO_LAUNCH_CHECK();
     return AAO_OK;
 }
@@ -442,7 +473,7 @@ static aao_status fgmres(Handle* h, const double* b, double* x, int x0_given, in
         red.nchunk = h->nchunk_for(1, rows * ((n0 + kWarp - 1) / kWarp));
         dim3 rgrid(red.nchunk, 1);
         const PtMap pmo = ptmap(n0);
-        const unsigned nbp = pt_blocks(pmo, rows), ntp = pt_threads(pmo);
+        const dim3 nbp = pt_grid(pmo, rows, 1), ntp = pt_block(pmo);
         while (true) {
             if (!std::isfinite(beta)) {
                 set_error("residual became non-finite");
@@ -740,7 +771,7 @@ aao_status aao_rk_rhs(aao_rk_handle hh, const double* f, int f_time_dep, const d
     AAO_TRY(stage_in(hh, u0, (size_t)h->nx, hh->stage_aux, &ud));
     double* od;
     AAO_TRY(stage_out_begin(rhs, hh->stage_out, &od));
-    launch(k_rhs, (unsigned)((h->nst + 255) / 256), 256, 0, h->stream, h->nx, h->nt, h->s, fd, f_time_dep, ud, od);
+    AAO_TRY(rhs_dev(h, fd, f_time_dep, ud, od));
     AAO_LAUNCH_CHECK();
     return stage_out_end(hh, rhs, od, (size_t)h->nst);
 }
@@ -817,7 +848,7 @@ aao_status aao_rk_solve(aao_rk_handle hh, const double* f, int f_time_dep, const
     const double *fd, *ud;
     AAO_TRY(stage_in(hh, f, f_time_dep ? (size_t)h->nt * h->s * h->nx : (size_t)h->nx, hh->stage_in, &fd));
     AAO_TRY(stage_in(hh, u0, (size_t)h->nx, hh->stage_aux, &ud));
-    launch(k_rhs, (unsigned)((h->nst + 255) / 256), 256, 0, h->stream, h->nx, h->nt, h->s, fd, f_time_dep, ud, h->rhs);
+    AAO_TRY(rhs_dev(h, fd, f_time_dep, ud, h->rhs));
     AAO_LAUNCH_CHECK();
     double* xd;
     AAO_TRY(stage_out_begin(x, hh->stage_out, &xd));
@@ -847,9 +878,22 @@ aao_status aao_rk_adjoint_solve(aao_rk_handle hh, const double* dJdx, double* la
     AAO_TRY(stage_out_begin(lambda, hh->stage_out, &ld));
     aao_status s = fgmres(h, bd, ld, 0, 1, info, hh->sd);
     if (s != AAO_OK && s != AAO_ERR_NOT_CONVERGED) return s;
+    if (grad_kappa && h->q1) {
+        set_error("grad_kappa is defined for the finite-difference discretisation only");
+        return AAO_ERR_UNSUPPORTED;
+    }
     if (grad_f) {
         double* gd = is_device_ptr(grad_f) ? grad_f : h->w;
-        launch(k_grad_f, (unsigned)((h->nx + 255) / 256), 256, 0, h->stream, h->nx, h->nt, h->s, ld, gd);
+        if (h->q1) {
+            // grad_f = M^T sum lambda_V = M sum lambda_V
+            launch(k_grad_f, (unsigned)((h->nx + 255) / 256), 256, 0, h->stream, h->nx, h->nt, h->s, (const double*)ld,
+                   h->xs);
+            const PtMap pm = ptmap(h->g.n0);
+            launch(k_apply_M_q1, pt_grid(pm, h->g.R, 1), pt_block(pm), 0, h->stream, h->g, pm, h->q1d,
+                   (const double*)h->xs, gd);
+        } else {
+            launch(k_grad_f, (unsigned)((h->nx + 255) / 256), 256, 0, h->stream, h->nx, h->nt, h->s, ld, gd);
+        }
         AAO_LAUNCH_CHECK();
         if (gd != grad_f) {
             AAO_CUDA_TRY(cudaMemcpyAsync(grad_f, gd, sizeof(double) * h->nx, cudaMemcpyDeviceToHost, h->stream));
@@ -861,7 +905,8 @@ aao_status aao_rk_adjoint_solve(aao_rk_handle hh, const double* dJdx, double* la
         const Geo& g = h->g;
         long long nnode = (long long)(g.n0 + 2) * (g.n1 + 2) * (g.d == 3 ? g.n2 + 2 : 1);
         double* gd = is_device_ptr(grad_kappa) ? grad_kappa : h->r;
-        launch(k_grad_kappa, (unsigned)((nnode + 127) / 128), 128, 0, h->stream, g, h->nt, h->tab, h->tau, ld, xd, gd);
+        launch(k_grad_kappa, (unsigned)((nnode + 127) / 128), 128, 0, h->stream, g, h->nt, h->tab, h->tau,
+               (const double*)ld, xd, gd, 0);
         AAO_LAUNCH_CHECK();
         if (gd != grad_kappa) {
             AAO_CUDA_TRY(cudaMemcpyAsync(grad_kappa, gd, sizeof(double) * nnode, cudaMemcpyDeviceToHost, h->stream));
@@ -870,6 +915,30 @@ aao_status aao_rk_adjoint_solve(aao_rk_handle hh, const double* dJdx, double* la
     aao_status s2 = stage_out_end(hh, lambda, ld, (size_t)h->nst);
     AAO_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return s != AAO_OK ? s : s2;
+}
+
+aao_status aao_rk_grad_kappa(aao_rk_handle hh, const double* lambda, const double* x_fwd, double* grad_kappa,
+                             int accumulate) {
+    H_CHECK(hh);
+    Handle* h = &hh->h;
+    if (!lambda || !x_fwd || !grad_kappa) {
+        set_error("null vector");
+        return AAO_ERR_ARG;
+    }
+    if (h->q1) {
+        set_error("grad_kappa is defined for the finite-difference discretisation only");
+        return AAO_ERR_UNSUPPORTED;
+    }
+    if (!is_device_ptr(lambda) || !is_device_ptr(x_fwd) || !is_device_ptr(grad_kappa)) {
+        set_error("aao_rk_grad_kappa takes device vectors");
+        return AAO_ERR_ARG;
+    }
+    const Geo& g = h->g;
+    long long nnode = (long long)(g.n0 + 2) * (g.n1 + 2) * (g.d == 3 ? g.n2 + 2 : 1);
+    launch(k_grad_kappa, (unsigned)((nnode + 127) / 128), 128, 0, h->stream, g, h->nt, h->tab, h->tau, lambda, x_fwd,
+           grad_kappa, accumulate ? 1 : 0);
+    AAO_LAUNCH_CHECK();
+    return AAO_OK;
 }
 
 aao_status aao_rk_solve_batched(int nprob, const aao_rk_handle* hs, const double* const* f, const double* const* u0,

@@ -208,3 +208,89 @@ def test_graph_replay_equals_eager_launches():
     assert np.array_equal(zt1, zt2)
     ref = P.apply(host(r))
     assert rel_max(z1, ref) <= 1e-4
+
+
+# ---- Q1 finite elements (M and K 9/27-point tensor stencils; M^{-1} by Chebyshev) ----
+Q1_SHAPES = [((10, 12), 3, "radau", 2), ((7, 6, 5), 2, "radau", 3), ((40, 36), 2, "gauss", 2)]
+
+
+def make_q1(ns, nt, method, s, prec="fp64", tol=1e-10):
+    from paper_2609_16863_gb300 import Solver
+    from paper_2609_16863_gb300.tableau import make as tab
+    from gpu_util import dev
+    dev()
+    S = Solver(ns, 1.0, nt, tableau=tab(method, s), prec_P=prec, inner_maxit=3, inner_tol=1e-6, mg_cycles=3,
+               mg_pre=2, mg_post=2, mg_omega=0.8, tol=tol, disc="q1")
+    op = build(ns, 1.0, nt, method, s, disc="q1")
+    P = Preconditioner(op, ns, 3, 1e-6, 3, 2, 2, 0.8, cheb_steps=20)
+    return S, op, P
+
+
+@pytest.mark.parametrize("ns,nt,method,s", Q1_SHAPES)
+def test_q1_operator_pieces(ns, nt, method, s):
+    S, op, P = make_q1(ns, nt, method, s)
+    x = synth.random_vector(op.n_st, 91)
+    assert rel_max(host(S.matvec(to_dev(x), zeros(op.n_st))), op.matvec(x)) <= 1e-13
+    assert rel_max(host(S.matvec(to_dev(x), zeros(op.n_st), transpose=True)), op.rmatvec(x)) <= 1e-13
+    u0 = synth.random_vector(op.nx, 1)
+    f = synth.random_vector(op.nx, 2)
+    assert rel_max(host(S.rhs(to_dev(f), to_dev(u0), zeros(op.n_st))), op.rhs(u0, f)) <= 1e-14
+    b = synth.random_vector(op.nx, 92)
+    assert rel_max(host(S.shifted_solve(0, to_dev(b), zeros(op.nx))), P.mg[0].solve(b, 3)) <= 1e-12
+    r = synth.random_vector(op.n_st, 93)
+    assert rel_max(host(S.precond_apply(to_dev(r), zeros(op.n_st))), P.apply(r)) <= 1e-11
+    assert rel_max(host(S.precond_apply(to_dev(r), zeros(op.n_st), transpose=True)), P.apply_T(r)) <= 1e-11
+
+
+@pytest.mark.parametrize("ns,nt,method,s", Q1_SHAPES)
+def test_q1_solve_matches_oracle(ns, nt, method, s):
+    S, op, _ = make_q1(ns, nt, method, s)
+    u0 = synth.gaussian_random_field(ns, 0.2, 1.0, synth.rng_for(12, "u0"))
+    f = synth.gaussian_random_field(ns, 0.2, 1.0, synth.rng_for(12, "f"))
+    x, info = S.solve(to_dev(f), to_dev(u0), zeros(op.n_st))
+    ref = oracle_solve(op, ns, op.rhs(u0, f), OracleOptions(tol=1e-10, inner_maxit=3, inner_tol=1e-6, omega=0.8))
+    assert info.converged and info.outer_its == ref.outer_its
+    assert np.linalg.norm(host(x) - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+
+
+def test_q1_fp32_solve_and_adjoint_grad_f():
+    from oracle.adjoint import adjoint_solve, grad_f, tracking_dJdx
+    ns, nt, s = (24, 24), 4, 3
+    S, op, _ = make_q1(ns, nt, "radau", s, prec="fp32", tol=1e-10)
+    u0 = synth.random_vector(op.nx, 3)
+    f = synth.random_vector(op.nx, 4)
+    x, info = S.solve(to_dev(f), to_dev(u0), zeros(op.n_st))
+    ref = oracle_solve(op, ns, op.rhs(u0, f), OracleOptions(tol=1e-13))
+    assert info.converged
+    assert np.linalg.norm(host(x) - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+    S64, _, _ = make_q1(ns, nt, "radau", s, tol=1e-12)
+    tgt = synth.random_vector(op.nx, 5)
+    g = tracking_dJdx(op, ref.x, tgt)
+    gf = zeros(op.nx)
+    S64.adjoint_solve(to_dev(g), zeros(op.n_st), grad_f=gf)
+    lam, _, _, _ = adjoint_solve(op, ns, g, tol=1e-12, inner_maxit=3, inner_tol=1e-6, omega=0.8)
+    assert rel_max(host(gf), grad_f(op, lam)) <= 1e-9
+
+
+@pytest.mark.parametrize("ns,prec,tol", [((48, 40), "bf16", 3e-2), ((48, 40), "fp16", 5e-3),
+                                         ((20, 18, 22), "bf16", 3e-2), ((96, 72), "fp16", 5e-3),
+                                         ((97, 33), "bf16", 3e-2)])
+def test_lowprec_vcycles_near_fp64(ns, prec, tol):
+    """16-bit storage with per-row power-of-two scaling (rows of n0 values, ragged n0):
+    three V-cycles stay within a few storage roundings of the FP64 oracle."""
+    S, op, P = make(ns, 2, "radau", 2, prec=prec)
+    for i in range(2):
+        b = synth.random_vector(op.nx, 110 + i)
+        x = host(S.shifted_solve(i, to_dev(b), zeros(op.nx)))
+        assert rel_max(x, P.mg[i].solve(b, 3)) <= tol
+
+
+@pytest.mark.parametrize("ns,prec", [((48, 40), "bf16"), ((20, 18, 22), "fp16"), ((97, 33), "fp16")])
+def test_lowprec_solve_ragged(ns, prec):
+    S, op, _ = make(ns, 4, "radau", 3, prec=prec, tol=1e-9, inner_maxit=3, inner_tol=1e-3)
+    u0 = synth.random_vector(op.nx, 7)
+    f = synth.random_vector(op.nx, 8)
+    x, info = S.solve(to_dev(f), to_dev(u0), zeros(op.n_st))
+    ref = oracle_solve(op, ns, op.rhs(u0, f), OracleOptions(tol=1e-13))
+    assert info.converged
+    assert np.linalg.norm(host(x) - ref.x) <= 1e-7 * np.linalg.norm(ref.x)

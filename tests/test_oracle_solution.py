@@ -93,3 +93,15 @@ def test_all_at_once_equals_sequential_kappa():
     xs = sequential_rk(op, u0, f)
     r = solve(op, ns, op.rhs(u0, f), OracleOptions(tol=1e-13))
     assert np.linalg.norm(r.x - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+def test_all_at_once_equals_sequential_q1():
+    # Q1 finite elements: M is the FE mass matrix in Eq. (update_solution) and in Theta_hat
+    ns = (9, 11)
+    op = build(ns, 1.0, 5, "radau", 2, disc="q1")
+    u0 = synth.random_vector(op.nx, 1)
+    f = synth.random_vector(op.nx, 2)
+    xs = sequential_rk(op, u0, f)
+    r = solve(op, ns, op.rhs(u0, f), OracleOptions(tol=1e-13))
+    assert r.converged
+    assert np.linalg.norm(r.x - xs) <= 1e-11 * np.linalg.norm(xs)
