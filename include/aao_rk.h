@@ -215,7 +215,7 @@ aao_status aao_rk_inner_solve(aao_rk_handle h, int nblocks, const double* r, dou
  * needs no handle and calls no allocating routine.  All scratch lives in one
  * fixed 5 MiB device array inside the library, which every GPU that loads the
  * library keeps until the process exits; grids above 65536 points (or whose
- * coarsest level exceeds 64 points) are rejected with AAO_ERR_ARG.  b and x
+ * coarsest level exceeds 256 points) are rejected with AAO_ERR_ARG.  b and x
  * are device memory (n_x values, host pointers are rejected), the work is
  * queued on `stream` (NULL = default stream).  The first call on a device looks
  * up the array's device address, so make it before any stream capture.  Every

@@ -13,8 +13,9 @@ not as code):
   the average of its two neighbours, a Dirichlet boundary neighbour
   (index 0 or N+1) counting as 0; P = tensor product of the 1D P's;
 * restriction R = P^T, coarse operator A_c = P^T A P (Galerkin);
-* coarsen all axes together while every axis keeps N_c >= 2; the coarsest
-  level is solved exactly (dense Cholesky);
+* coarsen all axes together while the level has more than COARSEST_MAX = 256
+  unknowns and every axis keeps N_c >= 2; the coarsest level is solved
+  exactly (dense Cholesky);
 * smoother: damped Jacobi x <- x + omega D^{-1} (b - A x), nu1 sweeps before
   and nu2 after the coarse correction;
 * a solve runs `cycles` V-cycles from a zero initial guess, so it is a
@@ -31,6 +32,9 @@ from functools import reduce
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
+
+
+COARSEST_MAX = 256   # a level with at most this many unknowns is solved exactly
 
 
 def coarse_size(n: int) -> int:
@@ -53,7 +57,7 @@ def interp_1d(n: int) -> sp.csr_matrix:
 def level_sizes(ns):
     """Per-level interior sizes, finest first."""
     sizes = [tuple(ns)]
-    while all(coarse_size(n) >= 2 for n in sizes[-1]):
+    while int(np.prod(sizes[-1])) > COARSEST_MAX and all(coarse_size(n) >= 2 for n in sizes[-1]):
         sizes.append(tuple(coarse_size(n) for n in sizes[-1]))
     return sizes
 

@@ -1,0 +1,571 @@
+// Cluster-resident multigrid for one 2D item (the Schur sweep's shifted
+// solves (M + c_i K) x = b, Sec. 5: three V-cycles per stage solve).
+//
+// The V-cycles of one shifted solve are a chain of ~30 dependent grid-wide
+// steps per cycle; as separate launches each step costs a launch latency.
+// Here one thread-block cluster (up to 16 CTAs, one per SM) runs all cycles:
+//   * every level above the coarsest is split by grid rows over the CTAs; a
+//     CTA keeps its rows of x (two ping-pong buffers), b, the stored stencil
+//     and the Jacobi weights in shared memory;
+//   * x / b rows are stored with a zero column on each side and a ghost row
+//     above and below the CTA's range, so stencils, restriction and
+//     interpolation read without bounds tests (the zeros stand for the
+//     Dirichlet boundary and add exact zeros);
+//   * a step that writes a CTA's first or last row also stores that row into
+//     the neighbouring CTA's ghost row (distributed shared memory, generic
+//     addresses from `mapa`), so after the cluster barrier that ends the step
+//     every read is local;
+//   * the level-l partition follows the finest one: coarse row J belongs to
+//     the CTA owning fine row 2J+1, so restriction and interpolation only ever
+//     touch one row beyond a CTA's range;
+//   * the coarsest level (at most a few hundred unknowns) is held whole by
+//     every CTA: each CTA restricts its right-hand side from all CTAs'
+//     residual rows, applies its own slice of rows of the dense inverse
+//     (staged once per launch) and gathers the other slices after a cluster
+//     barrier;
+//   * the Jacobi weights omega / a_PP are staged once per launch, so a sweep
+//     is x + w (b - A x) without a division.
+// Operator applications, residuals, restriction and interpolation follow the
+// level kernels in mg.cuh (same formulas and summation order); intermediate
+// vectors stay on chip in the arithmetic type.
+#pragma once
+
+#include "mg.cuh"
+
+namespace aao {
+
+constexpr int kClMax = 16;            // CTAs per cluster (16 needs the non-portable size)
+constexpr int kClThreads = 1024;
+
+template <class SI> struct ClCtx {
+    using A = typename PT<SI>::A;
+    int C, L, T;                          // cluster size, levels, T = L-1 (the replicated coarsest level)
+    int cycles, nu1, nu2;
+    A omega;
+    A sigma, c;                           // level 0 (FD): sigma I + c K
+    int fine0, has_faces;
+    Geo g[kMaxLevels];
+    unsigned magic[kMaxLevels];           // ceil(2^32 / n0_l): p / n0_l = umulhi(p, magic) for p*n0_l < 2^32
+    int rlo[kMaxLevels][kClMax + 1];      // distributed level l: CTA r owns rows [rlo[l][r], rlo[l][r+1])
+    int maxr[kMaxLevels];                 // rows per CTA in the shared-memory layout (n1 for l >= T)
+    int off[kMaxLevels];                  // A-element offset of level l's X0 | X1 | B, each (maxr+2) x (n0+2)
+    int soff[kMaxLevels];                 // A-element offset of level l's staged stencil (9 x maxr*n0; -1: none)
+    int woff[kMaxLevels];                 // A-element offset of omega / a_PP (maxr*n0; -1: coarsest)
+    int fxoff, fyoff;                     // level 0 faces: maxr rows of n0+1 | maxr+1 rows of n0
+    int cs[kClMax + 1];                   // coarsest rows [cs[r], cs[r+1]) of A_c^{-1} b are computed by CTA r
+    int dinv_off;                         // A-element offset of this CTA's rows of A_c^{-1} (max rows * nc)
+    int rowtab_off;                       // A-element offset (8-byte aligned) of the row table of level T-1
+    const A* fx;
+    const A* fy;
+    const SI* sten[kMaxLevels];
+    const float* sten_sc[kMaxLevels];
+    const A* Dinv;
+};
+
+// This CTA's share of a distributed level.
+template <class A> struct ClLev {
+    int a, nr;                // own rows [a, a + nr)
+    A* pu[3];                 // ghost row below the range of the previous non-empty CTA (buffers X0, X1, B;
+                              // first interior column), or nullptr
+    A* pd[3];                 // ghost row above the range of the next non-empty CTA
+};
+
+template <class SI> struct ClShared {
+    ClCtx<SI> t;
+    ClLev<typename PT<SI>::A> lv[kMaxLevels];
+    int rank;
+};
+
+__device__ __forceinline__ unsigned cl_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cl_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Barrier after a step: the cluster for distributed levels, the CTA for replicated ones.
+__device__ __forceinline__ void cl_step_sync(bool dist) {
+    if (dist) cl_sync();
+    else __syncthreads();
+}
+
+// Generic address of the same shared-memory location in CTA `rank` of the cluster.
+template <class T> __device__ __forceinline__ T* cl_map(T* p, unsigned rank) {
+    unsigned long long out;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(p), "r"(rank));
+    return reinterpret_cast<T*>(out);
+}
+
+__device__ __forceinline__ int cl_div(int p, unsigned magic) { return (int)__umulhi((unsigned)p, magic); }
+
+// One level as a step sees it, held in registers for the step's loop.
+template <class A> struct ClL {
+    int n0, n1, nr, a, ld, xs, cs;
+    unsigned magic;
+    A* X;                     // buffer 0 at (row -1, column -1); buffer k at X + k*xs; (lr, c) at (lr+1)*ld + c+1
+    const A* S;               // stored stencil (component stride cs = maxr*n0); nullptr: FD level 0
+    const A* W;               // omega / a_PP (index lr*n0 + c)
+    A *pu0, *pu1, *pu2;       // neighbours' ghost rows (see ClLev)
+    A *pd0, *pd1, *pd2;
+    A sigma, c, hx2, hy2;
+    const A* fx;              // staged faces of the FD level (nullptr: kappa = 1)
+    const A* fy;
+    __device__ __forceinline__ A* pu(int k) const { return k == 0 ? pu0 : (k == 1 ? pu1 : pu2); }
+    __device__ __forceinline__ A* pd(int k) const { return k == 0 ? pd0 : (k == 1 ? pd1 : pd2); }
+    __device__ __forceinline__ A* el(int k, int lr, int col) const { return X + k * xs + (lr + 1) * ld + col + 1; }
+    // store v at (lr, c) of buffer k and mirror the CTA's first / last row into the neighbours' ghost rows
+    __device__ __forceinline__ void put(int k, int lr, int col, A v) const {
+        *el(k, lr, col) = v;
+        if (lr == 0) {
+            A* q = pu(k);
+            if (q) q[col] = v;
+        }
+        if (lr == nr - 1) {
+            A* q = pd(k);
+            if (q) q[col] = v;
+        }
+    }
+};
+
+template <class SI>
+__device__ __forceinline__ ClL<typename PT<SI>::A> cl_level(const ClShared<SI>& S, typename PT<SI>::A* sm, int l) {
+    using A = typename PT<SI>::A;
+    const ClCtx<SI>& t = S.t;
+    ClL<A> v;
+    v.n0 = t.g[l].n0;
+    v.n1 = t.g[l].n1;
+    v.ld = v.n0 + 2;
+    v.xs = (t.maxr[l] + 2) * v.ld;
+    v.cs = t.maxr[l] * v.n0;
+    v.magic = t.magic[l];
+    const bool dist = l < t.T;
+    v.a = dist ? S.lv[l].a : 0;
+    v.nr = dist ? S.lv[l].nr : v.n1;
+    v.X = sm + t.off[l];
+    v.S = (l == 0 && t.fine0) || t.soff[l] < 0 ? nullptr : sm + t.soff[l];
+    v.W = t.woff[l] < 0 ? nullptr : sm + t.woff[l];
+    v.pu0 = dist ? S.lv[l].pu[0] : nullptr;
+    v.pu1 = dist ? S.lv[l].pu[1] : nullptr;
+    v.pu2 = dist ? S.lv[l].pu[2] : nullptr;
+    v.pd0 = dist ? S.lv[l].pd[0] : nullptr;
+    v.pd1 = dist ? S.lv[l].pd[1] : nullptr;
+    v.pd2 = dist ? S.lv[l].pd[2] : nullptr;
+    v.sigma = t.sigma;
+    v.c = t.c;
+    v.hx2 = A(t.g[0].hx2);
+    v.hy2 = A(t.g[0].hy2);
+    v.fx = t.has_faces ? sm + t.fxoff : nullptr;
+    v.fy = t.has_faces ? sm + t.fyoff : nullptr;
+    return v;
+}
+
+// (A x)_P at own point p = (lr, c); xm points at x(lr, c) in the padded layout.
+template <class A>
+__device__ __forceinline__ A cl_apply(const ClL<A>& v, int p, int lr, int c, const A* xm) {
+    const int ld = v.ld;
+    if (v.S == nullptr) {
+        const A uP = xm[0], uW = xm[-1], uE = xm[1], uS = xm[-ld], uN = xm[ld];
+        A K;
+        if (v.fx == nullptr) {
+            K = v.hx2 * (A(2) * uP - uW - uE) + v.hy2 * (A(2) * uP - uS - uN);
+        } else {
+            const A* fxr = v.fx + lr * (v.n0 + 1);
+            const A* fyr = v.fy + lr * v.n0;
+            K = fxr[c] * (uP - uW) + fxr[c + 1] * (uP - uE) + fyr[c] * (uP - uS) + fyr[c + v.n0] * (uP - uN);
+        }
+        return v.sigma * uP + v.c * K;
+    }
+    const A* Sp = v.S + p;
+    const int cs = v.cs;
+    A acc = A(0);
+    acc += Sp[0 * cs] * xm[-ld - 1];
+    acc += Sp[1 * cs] * xm[-ld];
+    acc += Sp[2 * cs] * xm[-ld + 1];
+    acc += Sp[3 * cs] * xm[-1];
+    acc += Sp[4 * cs] * xm[0];
+    acc += Sp[5 * cs] * xm[1];
+    acc += Sp[6 * cs] * xm[ld - 1];
+    acc += Sp[7 * cs] * xm[ld];
+    acc += Sp[8 * cs] * xm[ld + 1];
+    return acc;
+}
+
+// Damped Jacobi into buffer 1-kin: zero ? w b : x + w (b - A x), x = buffer kin.
+template <class A>
+__device__ __forceinline__ void cl_sweep(const ClL<A>& v, int kin, bool zero, int tid, int nthr) {
+    const int n0 = v.n0;
+    const int np = v.nr * n0;
+    for (int p = tid; p < np; p += nthr) {
+        const int lr = cl_div(p, v.magic);
+        const int c = p - lr * n0;
+        const A bp = *v.el(2, lr, c);
+        A val;
+        if (zero) {
+            val = v.W[p] * bp;
+        } else {
+            const A* xm = v.el(kin, lr, c);
+            val = xm[0] + v.W[p] * (bp - cl_apply(v, p, lr, c, xm));
+        }
+        v.put(1 - kin, lr, c, val);
+    }
+}
+
+// Residual b - A x of buffer kin into buffer 1 - kin.
+template <class A>
+__device__ __forceinline__ void cl_residual(const ClL<A>& v, int kin, int tid, int nthr) {
+    const int n0 = v.n0;
+    const int np = v.nr * n0;
+    for (int p = tid; p < np; p += nthr) {
+        const int lr = cl_div(p, v.magic);
+        const int c = p - lr * n0;
+        const A* xm = v.el(kin, lr, c);
+        v.put(1 - kin, lr, c, *v.el(2, lr, c) - cl_apply(v, p, lr, c, xm));
+    }
+}
+
+// b_c = P^T r (r = buffer kr of the fine level f) on the coarse rows this CTA computes.
+// any_row: the coarse level is the replicated coarsest; fine rows come from rowtab (row i of
+// buffer 0, first interior column, in the CTA that owns it).
+template <class A>
+__device__ __forceinline__ void cl_restrict(const ClL<A>& f, const ClL<A>& cv, int kr, bool any_row,
+                                            const A* const* rowtab, int tid, int nthr) {
+    const int n0c = cv.n0;
+    const int np = cv.nr * n0c;
+    for (int p = tid; p < np; p += nthr) {
+        const int lr = cl_div(p, cv.magic);
+        const int I = p - lr * n0c;
+        const int J = cv.a + lr;
+        A acc = A(0);
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int fj = 2 * J + 1 + dy;
+            const A wy = dy == 0 ? A(1) : A(0.5);
+            const A* row;
+            if (any_row) {
+                if (fj < 0 || fj >= f.n1) continue;
+                row = rowtab[fj] + kr * f.xs;
+            } else {
+                row = f.el(kr, fj - f.a, 0);          // own or ghost row (zero beyond the boundary)
+            }
+            const int fi = 2 * I + 1;
+            acc += A(0.5) * wy * row[fi - 1];
+            acc += A(1) * wy * row[fi];
+            acc += A(0.5) * wy * row[fi + 1];        // the zero column when fi + 1 == n0
+        }
+        cv.put(2, lr, I, acc);
+    }
+}
+
+// 1D interpolation of fine index F: injection from coarse j0, or the average of j0 and j1
+// (index -1 or nc: the zero ghost row / column at the boundary).
+__device__ __forceinline__ void cl_interp(int F, int& j0, int& j1, bool& inj) {
+    const int g = F + 1;                 // 1-based; coarse j sits at fine 2(j+1)
+    inj = (g & 1) == 0;
+    if (inj) {
+        j0 = g / 2 - 1;
+        j1 = j0;
+    } else {
+        j0 = (g - 1) / 2 - 1;
+        j1 = (g + 1) / 2 - 1;
+    }
+}
+
+// x_f (buffer kx) += P x_c (buffer kc) on the fine rows this CTA computes.
+template <class A>
+__device__ __forceinline__ void cl_prolong(const ClL<A>& f, const ClL<A>& cv, int kx, int kc, int tid, int nthr) {
+    const int n0 = f.n0;
+    const int np = f.nr * n0;
+    for (int p = tid; p < np; p += nthr) {
+        const int lr = cl_div(p, f.magic);
+        const int c = p - lr * n0;
+        int y0, y1, x0, x1;
+        bool yi, xi;
+        cl_interp(f.a + lr, y0, y1, yi);
+        cl_interp(c, x0, x1, xi);
+        // injection in a direction: one coarse index, the second term gets weight 0
+        const A wy = yi ? A(1) : A(0.5), wx = xi ? A(1) : A(0.5);
+        const A w00 = wy * wx, w01 = xi ? A(0) : w00, w10 = yi ? A(0) : w00, w11 = (xi || yi) ? A(0) : w00;
+        const A* r0 = cv.el(kc, y0 - cv.a, 0);
+        const A* r1 = cv.el(kc, y1 - cv.a, 0);
+        A acc = *f.el(kx, lr, c);
+        acc += w00 * r0[x0];
+        acc += w01 * r0[x1];
+        acc += w10 * r1[x0];
+        acc += w11 * r1[x1];
+        f.put(kx, lr, c, acc);
+    }
+}
+
+// All mg_cycles V-cycles of (M + c K) x = b for one item, b and x in global memory.
+template <class SI>
+__global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* __restrict__ ctx, const int* active,
+                                                              Vec<SI> bv, Vec<SI> xout) {
+    pdl_prologue();
+    using A = typename PT<SI>::A;
+    __shared__ ClShared<SI> S;
+    extern __shared__ __align__(16) unsigned char cl_smem[];
+    A* sm = reinterpret_cast<A*>(cl_smem);
+    if (active && !active[0]) return;         // the same decision in every CTA of the cluster
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    {
+        const int* src = reinterpret_cast<const int*>(ctx);
+        int* dst = reinterpret_cast<int*>(&S.t);
+        for (int i = tid; i < (int)(sizeof(ClCtx<SI>) / sizeof(int)); i += nthr) dst[i] = src[i];
+    }
+    __syncthreads();
+    const ClCtx<SI>& t = S.t;
+    const int rank = (int)cl_rank();
+    const int L = t.L, T = t.T;
+    if (tid == 0) S.rank = rank;
+    // zero every x / b buffer (the padding columns and boundary ghost rows stay zero)
+    {
+        const int end = t.off[L - 1] + 3 * (t.maxr[L - 1] + 2) * (t.g[L - 1].n0 + 2);
+        for (int i = tid; i < end; i += nthr) sm[i] = A(0);
+    }
+    if (tid < T) {
+        const int l = tid;
+        ClLev<A>& v = S.lv[l];
+        v.a = t.rlo[l][rank];
+        v.nr = t.rlo[l][rank + 1] - v.a;
+        int pr = rank - 1;
+        while (pr >= 0 && t.rlo[l][pr + 1] == t.rlo[l][pr]) --pr;
+        int nx = rank + 1;
+        while (nx < t.C && t.rlo[l][nx + 1] == t.rlo[l][nx]) ++nx;
+        const int ld = t.g[l].n0 + 2, xs = (t.maxr[l] + 2) * ld;
+        for (int k = 0; k < 3; ++k) {
+            v.pu[k] = nullptr;
+            v.pd[k] = nullptr;
+            if (v.nr > 0 && v.a > 0 && pr >= 0) {
+                const int cnt = t.rlo[l][pr + 1] - t.rlo[l][pr];     // its ghost row below is row cnt
+                v.pu[k] = cl_map(sm + t.off[l] + k * xs + (cnt + 1) * ld + 1, (unsigned)pr);
+            }
+            if (v.nr > 0 && v.a + v.nr < t.g[l].n1 && nx < t.C)
+                v.pd[k] = cl_map(sm + t.off[l] + k * xs + 1, (unsigned)nx);     // its ghost row -1
+        }
+    }
+    // row table of level T-1 (the restriction into the coarsest level reads every row of it)
+    const A** rowtab = reinterpret_cast<const A**>(sm + t.rowtab_off);
+    {
+        const int l = T - 1;
+        const int ld = t.g[l].n0 + 2;
+        for (int i = tid; i < t.g[l].n1; i += nthr) {
+            int r = 0;
+            while (r + 1 < t.C && t.rlo[l][r + 1] <= i) ++r;
+            A* q = sm + t.off[l] + (i - t.rlo[l][r] + 1) * ld + 1;
+            rowtab[i] = r == rank ? q : cl_map(q, (unsigned)r);
+        }
+    }
+    __syncthreads();
+    // ---- stage b, faces, stencils, Jacobi weights and this CTA's rows of the coarsest inverse
+    // (loads from global memory are issued in groups before the shared-memory stores)
+    {
+        constexpr int U = 4;
+        const Geo& g = t.g[0];
+        const int a = t.rlo[0][rank], nr = t.rlo[0][rank + 1] - a;
+        const int np0 = nr * g.n0, ld0 = g.n0 + 2, xs0 = (t.maxr[0] + 2) * ld0;
+        View<SI> bs = view_of(bv, 0, 0, g.n0);
+        A* B0 = sm + t.off[0] + 2 * xs0;
+        // rows a-1 .. a+nr of b (the ghost rows too: the residual of a zero guess is b)
+        const int nb0 = nr > 0 ? (nr + 2) * g.n0 : 0;
+        for (int p0 = tid; p0 < nb0; p0 += U * nthr) {
+            A v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int p = p0 + u * nthr;
+                const int lr = cl_div(p, t.magic[0]) - 1;
+                const int row = a + lr;
+                v[u] = p < nb0 && row >= 0 && row < g.n1 ? bs.at(row, p - (lr + 1) * g.n0) : A(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int p = p0 + u * nthr;
+                const int lr = cl_div(p, t.magic[0]) - 1;
+                if (p < nb0) B0[(lr + 1) * ld0 + p - (lr + 1) * g.n0 + 1] = v[u];
+            }
+        }
+        if (t.fine0) {
+            const int w = g.n0 + 1;
+            if (t.has_faces) {
+                const int nfx = nr * w, nfy = (nr + 1) * g.n0;
+                const A* fx = t.fx + (long long)a * w;
+                const A* fy = t.fy + (long long)a * g.n0;
+                for (int p0 = tid; p0 < nfx; p0 += U * nthr) {
+                    A v[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) v[u] = p0 + u * nthr < nfx ? fx[p0 + u * nthr] : A(0);
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (p0 + u * nthr < nfx) sm[t.fxoff + p0 + u * nthr] = v[u];
+                }
+                for (int p0 = tid; p0 < nfy; p0 += U * nthr) {
+                    A v[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) v[u] = p0 + u * nthr < nfy ? fy[p0 + u * nthr] : A(0);
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (p0 + u * nthr < nfy) sm[t.fyoff + p0 + u * nthr] = v[u];
+                }
+            }
+            for (int p0 = tid; p0 < np0; p0 += U * nthr) {
+                A kd[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int p = p0 + u * nthr;
+                    const int lr = cl_div(p, t.magic[0]);
+                    const int c = p - lr * g.n0;
+                    if (t.has_faces && p < np0) {
+                        const long long fxi = (long long)(a + lr) * w + c, fyi = (long long)(a + lr) * g.n0 + c;
+                        kd[u] = t.fx[fxi] + t.fx[fxi + 1] + t.fy[fyi] + t.fy[fyi + g.n0];
+                    } else {
+                        kd[u] = A(2) * A(g.hx2) + A(2) * A(g.hy2);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (p0 + u * nthr < np0) sm[t.woff[0] + p0 + u * nthr] = t.omega / (t.sigma + t.c * kd[u]);
+            }
+        }
+        for (int l = t.fine0 ? 1 : 0; l < L - 1; ++l) {
+            const Geo& gl = t.g[l];
+            const bool dist = l < T;
+            const int al = dist ? t.rlo[l][rank] : 0;
+            const int npl = dist ? (t.rlo[l][rank + 1] - al) * gl.n0 : (int)gl.nx;
+            const int cs = t.maxr[l] * gl.n0;
+            const SI* src = t.sten[l] + (long long)al * gl.n0;
+            for (int p = tid; p < npl; p += nthr) {
+                A v[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) v[q] = PT<SI>::ld(src[(long long)q * gl.nx + p]);
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    if constexpr (PT<SI>::scaled) v[q] *= t.sten_sc[l][q];
+                    sm[t.soff[l] + q * cs + p] = v[q];
+                }
+                sm[t.woff[l] + p] = t.omega / v[4];
+            }
+        }
+        {
+            const int nc = (int)t.g[L - 1].nx;
+            const int n = (t.cs[rank + 1] - t.cs[rank]) * nc;
+            const A* src = t.Dinv + (long long)t.cs[rank] * nc;
+            for (int p0 = tid; p0 < n; p0 += U * nthr) {
+                A v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) v[u] = p0 + u * nthr < n ? src[p0 + u * nthr] : A(0);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (p0 + u * nthr < n) sm[t.dinv_off + p0 + u * nthr] = v[u];
+            }
+        }
+    }
+    __syncthreads();
+    cl_sync();     // every CTA of the cluster is resident and staged before any remote access
+    unsigned cur = 0u;       // bit l: buffer of level l holding the iterate
+    for (int cyc = 0; cyc < t.cycles; ++cyc) {
+        bool zero = cyc == 0;
+        // ---- down: distributed levels (l < T) step with cluster barriers, replicated ones with
+        // block barriers
+        for (int l = 0; l < L - 1; ++l) {
+            const bool dist = l < T;
+            const ClL<A> f = cl_level(S, sm, l);
+            int k = (cur >> l) & 1u;
+            for (int sw = 0; sw < t.nu1; ++sw) {
+                cl_sweep(f, k, zero && sw == 0, tid, nthr);
+                k ^= 1;
+                cl_step_sync(dist);
+            }
+            int kr;
+            if (zero && t.nu1 == 0) {
+                kr = 2;                                   // x = 0: the residual is b
+                cl_step_sync(dist);                       // b rows were written by this level's restriction
+            } else {
+                cl_residual(f, k, tid, nthr);
+                kr = k ^ 1;
+                cl_step_sync(dist);
+            }
+            cur = (cur & ~(1u << l)) | ((unsigned)k << l);
+            const ClL<A> cv = cl_level(S, sm, l + 1);
+            cl_restrict(f, cv, kr, dist && l + 1 >= T, rowtab, tid, nthr);
+            __syncthreads();
+            zero = true;
+        }
+        // ---- coarsest level, held whole by every CTA: x = A_c^{-1} b, this CTA's rows one warp
+        // per row, then the other CTAs' rows gathered after a cluster barrier
+        {
+            const int l = L - 1;
+            const ClL<A> v = cl_level(S, sm, l);
+            const int nc = v.n0 * v.n1;
+            const int k = (cur >> l) & 1u;
+            A* bvec = v.X + (1 - k) * v.xs;           // b of the coarsest level, unpadded copy
+            for (int p = tid; p < nc; p += nthr) {
+                const int lr = cl_div(p, v.magic);
+                bvec[p] = *v.el(2, lr, p - lr * v.n0);
+            }
+            __syncthreads();
+            const A* Di = sm + t.dinv_off;
+            const int lo = t.cs[rank], hi = t.cs[rank + 1];
+            const int w = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+            for (int p = lo + w; p < hi; p += nw) {
+                const A* row = Di + (p - lo) * nc;
+                A acc = A(0);
+                for (int q = lane; q < nc; q += kWarp) acc += row[q] * bvec[q];
+                acc = warp_sum(acc);
+                if (lane == 0) {
+                    const int lr = cl_div(p, v.magic);
+                    *v.el(k, lr, p - lr * v.n0) = acc;
+                }
+            }
+            cl_sync();
+            for (int p = tid; p < nc; p += nthr) {
+                if (p >= lo && p < hi) continue;
+                int r = 0;
+                while (r + 1 < t.C && t.cs[r + 1] <= p) ++r;
+                const int lr = cl_div(p, v.magic);
+                A* q = v.el(k, lr, p - lr * v.n0);
+                *q = *cl_map(q, (unsigned)r);
+            }
+            __syncthreads();
+        }
+        // ---- up
+        for (int l = L - 2; l >= 0; --l) {
+            const bool dist = l < T;
+            const ClL<A> f = cl_level(S, sm, l);
+            const ClL<A> cv = cl_level(S, sm, l + 1);
+            int k = (cur >> l) & 1u;
+            cl_prolong(f, cv, k, (cur >> (l + 1)) & 1u, tid, nthr);
+            cl_step_sync(dist);
+            for (int sw = 0; sw < t.nu2; ++sw) {
+                cl_sweep(f, k, false, tid, nthr);
+                k ^= 1;
+                cl_step_sync(dist);
+            }
+            cur = (cur & ~(1u << l)) | ((unsigned)k << l);
+        }
+    }
+    // ---- write this CTA's rows of x_0
+    {
+        const ClL<A> v = cl_level(S, sm, 0);
+        const int k = cur & 1u;
+        if constexpr (PT<SI>::scaled) {
+            const int w = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+            for (int lr = w; lr < v.nr; lr += nw) {
+                SI* o;
+                float* osc;
+                row_store_ptrs(xout, 0, 0, v.a + lr, v.n0, o, osc);
+                const A* X = v.el(k, lr, 0);
+                row_store<SI>(o, osc, v.n0, lane, [&](int c) -> A { return X[c]; });
+            }
+        } else {
+            SI* o = xout.d + (long long)v.a * v.n0;
+            for (int p = tid; p < v.nr * v.n0; p += nthr) {
+                const int lr = cl_div(p, v.magic);
+                o[p] = PT<SI>::st(*v.el(k, lr, p - lr * v.n0));
+            }
+        }
+    }
+}
+
+}  // namespace aao

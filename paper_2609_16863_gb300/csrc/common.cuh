@@ -25,6 +25,7 @@ constexpr int kMaxInner = 16;            // inner GMRES iterations
 constexpr int kMaxRestart = 64;          // outer FGMRES restart
 constexpr int kMaxLevels = 16;
 constexpr int kMaxCoarsest = 512;        // unknowns of the dense coarsest solve
+constexpr int kCoarsestTarget = 256;     // coarsening stops at the first level with at most this many unknowns
 constexpr int kPtMaxThreads = 512;       // threads per CTA of the point-mapped row kernels
 
 // ---------------------------------------------------------------------------
@@ -433,6 +434,33 @@ inline void launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t shmem, cud
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+    if (slot >= 0) prof_end_launch(slot, st);
+}
+
+// The same for a grid of thread-block clusters of `cluster` CTAs along x.
+template <class... KArgs, class... Args>
+inline void launch_cluster(void (*k)(KArgs...), dim3 grid, dim3 block, size_t shmem, cudaStream_t st, int cluster,
+                           Args... args) {
+    ++g_launches;
+    ++g_thread_launches;
+    double bytes = g_bytes_hint;
+    g_bytes_hint = 0.0;
+    int slot = g_prof_on ? prof_begin_launch((const void*)k, st, bytes) : -1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = shmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = (unsigned)cluster;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
     cudaLaunchKernelEx(&cfg, k, args...);
     if (slot >= 0) prof_end_launch(slot, st);
 }

@@ -41,13 +41,20 @@ __device__ __forceinline__ void block_finish(double v, int b, const Red& red, do
         last = (prev == (unsigned int)red.nchunk - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {            // the whole block sums the partials (fixed order: strided, warp, then warps)
         __threadfence();
         double t = 0.0;
         const volatile double* p = red.partials + (long long)b * red.nchunk;
-        for (int i = 0; i < red.nchunk; ++i) t += p[i];
-        *out = do_sqrt ? sqrt(t) : t;
-        red.count[b] = 0;
+        for (int i = threadIdx.x; i < red.nchunk; i += blockDim.x) t += p[i];
+        t = warp_sum(t);
+        if (lane_id() == 0) sh[w] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int i = 0; i < kWarpsPerBlock; ++i) s += sh[i];
+            *out = do_sqrt ? sqrt(s) : s;
+            red.count[b] = 0;
+        }
     }
 }
 

@@ -705,7 +705,8 @@ __device__ __forceinline__ LevelOp<SI> tail_op(const TailCtx<SI>& t, int l, cons
 // buffers (one barrier per sweep); cur selects the buffer holding x.
 template <class SI>
 __device__ __forceinline__ void tail_smooth(const TailCtx<SI>& t, int l, typename PT<SI>::A* sm, int sweeps,
-                                            bool zero_first, int& cur) {
+                                            bool zero_first, unsigned& curbits) {
+    int cur = (curbits >> l) & 1u;
     using A = typename PT<SI>::A;
     const LevelOp<SI> op = tail_op(t, l, reinterpret_cast<const unsigned char*>(sm));
     const Geo& g = op.g;
@@ -733,6 +734,7 @@ __device__ __forceinline__ void tail_smooth(const TailCtx<SI>& t, int l, typenam
         cur = 1 - cur;
         __syncthreads();
     }
+    curbits = (curbits & ~(1u << l)) | ((unsigned)cur << l);
 }
 
 template <class SI>
@@ -747,8 +749,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
     const int nt = blockDim.x, tid = threadIdx.x;
     const int lc = t.lc, L = t.L;
     // per level: X0, X1 (x ping-pong; the free one holds the residual), B
-    int cur[kMaxLevels];
-    for (int l = 0; l < kMaxLevels; ++l) cur[l] = 0;
+    unsigned cur = 0u;      // bit l: which of level l's two x buffers holds the iterate
     // copy the coarse stencils of levels >= stage_from into shared memory
     for (int l = t.stage_from; l < L; ++l) {
         if (l < 1) continue;
@@ -776,12 +777,12 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
         const Geo& gf = op.g;
         const Geo& gc = t.op[l + 1].g;
         if (t.nu1 > 0) {
-            tail_smooth(t, l, sm, t.nu1, xzero, cur[l]);
+            tail_smooth(t, l, sm, t.nu1, xzero, cur);
             xzero = false;
         }
         A* X0 = sm + t.off[l];
-        const A* Xf = X0 + (long long)cur[l] * gf.nx;
-        A* Rf = X0 + (long long)(1 - cur[l]) * gf.nx;   // the free x buffer holds the residual
+        const A* Xf = X0 + (long long)((cur >> (l)) & 1u) * gf.nx;
+        A* Rf = X0 + (long long)(1 - ((cur >> (l)) & 1u)) * gf.nx;   // the free x buffer holds the residual
         const A* Bv = X0 + 2 * gf.nx;
         A* Xc = sm + t.off[l + 1];
         A* Bc = Xc + 2 * gc.nx;
@@ -832,7 +833,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
     }
     {
         const Geo& g = t.op[L - 1].g;
-        A* X = sm + t.off[L - 1] + (long long)cur[L - 1] * g.nx;
+        A* X = sm + t.off[L - 1] + (long long)((cur >> (L - 1)) & 1u) * g.nx;
         const A* Bv = sm + t.off[L - 1] + 2 * g.nx;
         const int nc = (int)g.nx;
         for (int p = tid; p < nc; p += nt) {
@@ -845,8 +846,8 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
     for (int l = L - 2; l >= lc; --l) {
         const Geo& gf = t.op[l].g;
         const Geo& gc = t.op[l + 1].g;
-        A* X = sm + t.off[l] + (long long)cur[l] * gf.nx;
-        const A* Xc = sm + t.off[l + 1] + (long long)cur[l + 1] * gc.nx;
+        A* X = sm + t.off[l] + (long long)((cur >> (l)) & 1u) * gf.nx;
+        const A* Xc = sm + t.off[l + 1] + (long long)((cur >> (l + 1)) & 1u) * gc.nx;
         for (int p = tid; p < gf.nx; p += nt) {
             int c = p % gf.n0;
             long long row = p / gf.n0;
@@ -865,12 +866,12 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailCtx<SI> t, int B, cons
             X[p] = acc;
         }
         __syncthreads();
-        if (t.nu2 > 0) tail_smooth(t, l, sm, t.nu2, false, cur[l]);
+        if (t.nu2 > 0) tail_smooth(t, l, sm, t.nu2, false, cur);
     }
     // write level lc
     {
         const Geo& g = t.op[lc].g;
-        const A* X = sm + t.off[lc] + (long long)cur[lc] * g.nx;
+        const A* X = sm + t.off[lc] + (long long)((cur >> (lc)) & 1u) * g.nx;
         const int w = tid >> 5, lane = tid & 31, nw = nt >> 5;
         for (long long row = w; row < g.R; row += nw) {
             SI* o;
@@ -919,7 +920,8 @@ __device__ __forceinline__ typename PT<SI>::A tail2d_apply(const LevelOp<SI>& op
 
 template <class SI>
 __device__ __forceinline__ void tail2d_smooth(const TailCtx<SI>& t, int l, typename PT<SI>::A* sm, int sweeps,
-                                              bool zero_first, int& cur) {
+                                              bool zero_first, unsigned& curbits) {
+    int cur = (curbits >> l) & 1u;
     using A = typename PT<SI>::A;
     const LevelOp<SI> op = tail_op(t, l, reinterpret_cast<const unsigned char*>(sm));
     const Geo& g = op.g;
@@ -943,6 +945,7 @@ __device__ __forceinline__ void tail2d_smooth(const TailCtx<SI>& t, int l, typen
         cur = 1 - cur;
         __syncthreads();
     }
+    curbits = (curbits & ~(1u << l)) | ((unsigned)cur << l);
 }
 
 template <class SI>
@@ -957,8 +960,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail_2d(TailCtx<SI> t, int B, c
     const int tx = threadIdx.x, ty = threadIdx.y, bx = blockDim.x, by = blockDim.y;
     const int tid = ty * bx + tx, nt = bx * by;
     const int lc = t.lc, L = t.L;
-    int cur[kMaxLevels];
-    for (int l = 0; l < kMaxLevels; ++l) cur[l] = 0;
+    unsigned cur = 0u;      // bit l: which of level l's two x buffers holds the iterate
     for (int l = t.stage_from; l < L; ++l) {
         if (l < 1) continue;
         const int n = t.op[l].ncoef * (int)t.op[l].g.nx;
@@ -986,12 +988,12 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail_2d(TailCtx<SI> t, int B, c
         const Geo& gf = op.g;
         const Geo& gc = t.op[l + 1].g;
         if (t.nu1 > 0) {
-            tail2d_smooth(t, l, sm, t.nu1, xzero, cur[l]);
+            tail2d_smooth(t, l, sm, t.nu1, xzero, cur);
             xzero = false;
         }
         A* X0 = sm + t.off[l];
-        const A* Xf = X0 + (long long)cur[l] * gf.nx;
-        A* Rf = X0 + (long long)(1 - cur[l]) * gf.nx;
+        const A* Xf = X0 + (long long)((cur >> (l)) & 1u) * gf.nx;
+        A* Rf = X0 + (long long)(1 - ((cur >> (l)) & 1u)) * gf.nx;
         const A* Bv = X0 + 2 * gf.nx;
         for (int j = ty; j < gf.n1; j += by)
             for (int c = tx; c < gf.n0; c += bx) {
@@ -1030,7 +1032,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail_2d(TailCtx<SI> t, int B, c
     }
     {
         const Geo& g = t.op[L - 1].g;
-        A* X = sm + t.off[L - 1] + (long long)cur[L - 1] * g.nx;
+        A* X = sm + t.off[L - 1] + (long long)((cur >> (L - 1)) & 1u) * g.nx;
         const A* Bv = sm + t.off[L - 1] + 2 * g.nx;
         const int nc = (int)g.nx;
         for (int p = tid; p < nc; p += nt) {
@@ -1043,8 +1045,8 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail_2d(TailCtx<SI> t, int B, c
     for (int l = L - 2; l >= lc; --l) {
         const Geo& gf = t.op[l].g;
         const Geo& gc = t.op[l + 1].g;
-        A* X = sm + t.off[l] + (long long)cur[l] * gf.nx;
-        const A* Xc = sm + t.off[l + 1] + (long long)cur[l + 1] * gc.nx;
+        A* X = sm + t.off[l] + (long long)((cur >> (l)) & 1u) * gf.nx;
+        const A* Xc = sm + t.off[l + 1] + (long long)((cur >> (l + 1)) & 1u) * gc.nx;
         for (int j = ty; j < gf.n1; j += by) {
             int Jy[2];
             float wy[2];
@@ -1060,11 +1062,11 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail_2d(TailCtx<SI> t, int B, c
             }
         }
         __syncthreads();
-        if (t.nu2 > 0) tail2d_smooth(t, l, sm, t.nu2, false, cur[l]);
+        if (t.nu2 > 0) tail2d_smooth(t, l, sm, t.nu2, false, cur);
     }
     {
         const Geo& g = t.op[lc].g;
-        const A* X = sm + t.off[lc] + (long long)cur[lc] * g.nx;
+        const A* X = sm + t.off[lc] + (long long)((cur >> (lc)) & 1u) * g.nx;
         const int w = tid >> 5, lane = tid & 31, nw = nt >> 5;
         for (long long row = w; row < g.R; row += nw) {
             SI* o;

@@ -19,7 +19,7 @@ namespace aao {
 // grids of up to 40^3 points (kNoAllocMaxPoints), with the hierarchy below.
 constexpr long long kNoAllocDoubles = 655360;
 constexpr long long kNoAllocMaxPoints = 65536;
-constexpr int kNoAllocMaxCoarsest = 64;
+constexpr int kNoAllocMaxCoarsest = kCoarsestTarget;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 // Device address of g_noalloc_scratch per device, looked up once per device.
@@ -103,13 +103,14 @@ extern "C" aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double 
         set_error("b and x must be device memory");
         return AAO_ERR_ARG;
     }
-    // levels: coarsen every axis while each keeps N/2 >= 2 (same hierarchy as the handle path)
+    // levels: coarsen every axis while the level has more than kCoarsestTarget points and each
+    // axis keeps N/2 >= 2 (same hierarchy as the handle path)
     Geo lev[kMaxLevels];
     int L = 0;
     Geo cur = g;
     while (true) {
         lev[L++] = cur;
-        bool more = cur.n0 / 2 >= 2 && cur.n1 / 2 >= 2 && (cur.d == 2 || cur.n2 / 2 >= 2);
+        bool more = cur.nx > kCoarsestTarget && cur.n0 / 2 >= 2 && cur.n1 / 2 >= 2 && (cur.d == 2 || cur.n2 / 2 >= 2);
         if (!more || L == kMaxLevels) break;
         Geo nx = cur;
         nx.n0 = cur.n0 / 2;

@@ -12,8 +12,11 @@
 //             z_V = Theta_tilde^{-T} (r_V + tau (b (x) M) z_{v,n+1}).
 #pragma once
 
+#include <algorithm>
+#include <cstring>
 #include <type_traits>
 
+#include "cluster_mg.cuh"
 #include "handle.cuh"
 #include "mg.cuh"
 
@@ -73,6 +76,10 @@ class Precond : public PrecondBase {
     };
     Tail tails[2];                 // [0]: B == 1, [1]: B > 1
     int tail_threads = 1024;
+    // Cluster-resident shifted solves for single 2D items (the Schur sweep).
+    int cl_C = 0;                  // CTAs per cluster; 0: not used for this problem
+    size_t cl_smem = 0;
+    ClCtx<SI>* cl_ctx = nullptr;   // device, one context per stage
     int* hact = nullptr;           // pinned mirror of activeh (profiling)
 
     cudaStream_t cur_stream = nullptr;     // stream of the next launch (capture stream while capturing)
@@ -136,7 +143,7 @@ class Precond : public PrecondBase {
         while (true) {
             lev[L].g = g;
             ++L;
-            bool more = g.n0 / 2 >= 2 && g.n1 / 2 >= 2 && (g.d == 2 || g.n2 / 2 >= 2);
+            bool more = g.nx > kCoarsestTarget && g.n0 / 2 >= 2 && g.n1 / 2 >= 2 && (g.d == 2 || g.n2 / 2 >= 2);
             if (!more || L == kMaxLevels) break;
             Geo c = g;
             c.n0 = g.n0 / 2;
@@ -263,6 +270,7 @@ class Precond : public PrecondBase {
         // opt-in maximum so that handles with larger tails keep working
         AAO_CUDA_TRY(cudaFuncSetAttribute(k_vcycle_tail<SI>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         AAO_CUDA_TRY(cudaFuncSetAttribute(k_vcycle_tail_2d<SI>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        AAO_TRY(build_cluster(optin));
         // ---- level scratch
         for (int l = 0; l < L; ++l) {
             const Geo& gl = lev[l].g;
@@ -368,6 +376,112 @@ class Precond : public PrecondBase {
             t.omega = (A)h->opt.mg_omega;
             t.nu1 = h->opt.mg_pre;
             t.nu2 = h->opt.mg_post;
+        }
+        return AAO_OK;
+    }
+
+    // Plan the cluster-resident shifted solve: 2D, at least one level above the
+    // coarsest, everything of a CTA's rows within its shared memory, and one
+    // cluster of 16 (else 8) CTAs co-resident on the device.
+    aao_status build_cluster(int optin) {
+        cl_C = 0;
+        const Geo& g0 = h->g;
+        if (g0.d != 2 || L < 2) return AAO_OK;
+        const int T = L - 1;
+        cudaFuncAttributes fa;
+        AAO_CUDA_TRY(cudaFuncGetAttributes(&fa, k_cluster_mg<SI>));
+        const long long dyn_max = (long long)optin - (long long)fa.sharedSizeBytes;
+        if (dyn_max <= 0) return AAO_OK;
+        AAO_CUDA_TRY(cudaFuncSetAttribute(k_cluster_mg<SI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max));
+        AAO_CUDA_TRY(cudaFuncSetAttribute(k_cluster_mg<SI>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        const bool fine0 = !h->q1;
+        const bool faces = fine0 && h->has_kappa;
+        for (int C : {16, 8}) {
+            if (g0.n1 < C) continue;
+            ClCtx<SI> t;
+            std::memset(&t, 0, sizeof(t));
+            t.C = C;
+            t.L = L;
+            t.T = T;
+            t.cycles = h->opt.mg_cycles;
+            t.nu1 = h->opt.mg_pre;
+            t.nu2 = h->opt.mg_post;
+            t.omega = (A)h->opt.mg_omega;
+            t.sigma = A(1);
+            t.fine0 = fine0 ? 1 : 0;
+            t.has_faces = faces ? 1 : 0;
+            t.fx = facesA.fx;
+            t.fy = facesA.fy;
+            long long o = 0;
+            auto take = [&](long long n) {
+                long long at = o;
+                o += (n + 3) / 4 * 4;
+                return (int)at;
+            };
+            for (int l = 0; l < L; ++l) {
+                const Geo& gl = lev[l].g;
+                t.g[l] = gl;
+                t.magic[l] = (unsigned)((4294967296ULL + (unsigned long long)gl.n0 - 1) / (unsigned long long)gl.n0);
+                if (l < T) {
+                    for (int r = 0; r <= C; ++r)
+                        t.rlo[l][r] = l == 0 ? (int)((long long)r * gl.n1 / C) : t.rlo[l - 1][r] / 2;
+                    int mr = 0;
+                    for (int r = 0; r < C; ++r) mr = std::max(mr, t.rlo[l][r + 1] - t.rlo[l][r]);
+                    t.maxr[l] = std::max(mr, 1);
+                } else {
+                    t.maxr[l] = gl.n1;
+                }
+                t.off[l] = take(3LL * (t.maxr[l] + 2) * (gl.n0 + 2));
+            }
+            for (int l = 0; l < L; ++l) {
+                t.soff[l] = t.woff[l] = -1;
+                if ((l >= 1 || !fine0) && l < L - 1) t.soff[l] = take(9LL * t.maxr[l] * lev[l].g.n0);
+                if (l < L - 1) t.woff[l] = take((long long)t.maxr[l] * lev[l].g.n0);
+            }
+            t.fxoff = t.fyoff = -1;
+            if (faces) {
+                t.fxoff = take((long long)t.maxr[0] * (g0.n0 + 1));
+                t.fyoff = take((long long)(t.maxr[0] + 1) * g0.n0);
+            }
+            const long long ncst = lev[L - 1].g.nx;
+            int msl = 0;
+            for (int r = 0; r <= C; ++r) t.cs[r] = (int)((long long)r * ncst / C);
+            for (int r = 0; r < C; ++r) msl = std::max(msl, t.cs[r + 1] - t.cs[r]);
+            t.dinv_off = take((long long)msl * ncst);
+            t.rowtab_off = take(((long long)lev[T - 1].g.n1 * (long long)sizeof(void*) + sizeof(A) - 1) / sizeof(A));
+            const long long bytes = o * (long long)sizeof(A);
+            if (bytes > dyn_max) continue;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(C);
+            cfg.blockDim = dim3(kClThreads);
+            cfg.dynamicSmemBytes = (size_t)bytes;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)C;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, k_cluster_mg<SI>, &cfg) != cudaSuccess || nclusters < 1) {
+                cudaGetLastError();
+                continue;
+            }
+            ClCtx<SI> hc[kMaxS];
+            for (int i = 0; i < h->s; ++i) {
+                hc[i] = t;
+                hc[i].c = (A)(h->tau * h->D[i]);
+                for (int l = 0; l < L; ++l) {
+                    hc[i].sten[l] = lev[l].sten[i];
+                    hc[i].sten_sc[l] = lev[l].sten_sc[i];
+                }
+                hc[i].Dinv = Dinv[i];
+            }
+            AAO_TRY(ar.alloc(&cl_ctx, (size_t)h->s));
+            AAO_CUDA_TRY(cudaMemcpy(cl_ctx, hc, sizeof(ClCtx<SI>) * h->s, cudaMemcpyHostToDevice));
+            cl_C = C;
+            cl_smem = (size_t)bytes;
+            return AAO_OK;
         }
         return AAO_OK;
     }
@@ -549,6 +663,13 @@ class Precond : public PrecondBase {
     }
 
     aao_status mg_solve(int stage, int B, const int* act, Vec<SI> b, Vec<SI> out) {
+        if (B == 1 && cl_C > 0) {
+            bytes_hint(2.0 * nact * h->g.nx * sizeof(SI));
+            launch_cluster(k_cluster_mg<SI>, dim3((unsigned)cl_C), dim3(kClThreads), cl_smem, st(), cl_C,
+                           (const ClCtx<SI>*)(cl_ctx + stage), act, b, out);
+            AAO_LAUNCH_CHECK();
+            return AAO_OK;
+        }
         Vec<SI> zero{};
         for (int cyc = 0; cyc < h->opt.mg_cycles; ++cyc) AAO_TRY(vcycle(0, stage, B, act, cyc == 0 ? zero : out, b, out));
         return AAO_OK;

@@ -101,25 +101,29 @@ def test_interp_1d_small():
     assert np.array_equal(P4, [[0.5, 0], [1, 0], [0.5, 0.5], [0, 1]])
     P5 = interp_1d(5).toarray()
     assert np.array_equal(P5, [[0.5, 0], [1, 0], [0.5, 0.5], [0, 1], [0, 0.5]])
-    assert level_sizes((32, 32)) == [(32, 32), (16, 16), (8, 8), (4, 4), (2, 2)]
-    assert level_sizes((96,) * 3)[-1] == (3, 3, 3) and len(level_sizes((96,) * 3)) == 6
+    # coarsening stops at the first level with <= 256 unknowns, or when an axis cannot be halved
+    assert level_sizes((32, 32)) == [(32, 32), (16, 16)]
+    assert level_sizes((256, 256))[-1] == (16, 16) and len(level_sizes((256, 256))) == 5
+    assert level_sizes((96,) * 3) == [(96,) * 3, (48,) * 3, (24,) * 3, (12,) * 3, (6,) * 3]
+    assert level_sizes((300, 4)) == [(300, 4), (150, 2)]
+    assert level_sizes((15, 17)) == [(15, 17)]
 
 
 def test_galerkin_closed_form():
     # constant coefficients, N = 2^k - 1: P^T (I (x) K1 + K1 (x) I) P has the interior
     # stencil (P1^T K1 P1) (x) (P1^T P1) + (P1^T P1) (x) (P1^T K1 P1) with
     # P1^T K1 P1 = (1/(2 h^2)) tridiag(-1, 2, -1) and P1^T P1 = tridiag(1/4, 3/2, 1/4).
-    N, c = 15, 0.3
+    N, c = 31, 0.3
     ns = (N, N)
     op = build(ns, 1.0, 1, "radau", 1)
     A0 = (sp.identity(N * N) + c * op.K).tocsr()
     H = Hierarchy(A0, ns)
-    Ac = H.A[1].toarray().reshape(7, 7, 7, 7)
-    h = 1.0 / 16
+    Ac = H.A[1].toarray().reshape(15, 15, 15, 15)
+    h = 1.0 / 32
     k1 = np.array([-1.0, 2.0, -1.0]) / (2 * h * h)
     m1 = np.array([0.25, 1.5, 0.25])
     sten = np.outer(m1, m1) + c * (np.outer(k1, m1) + np.outer(m1, k1))
-    assert np.allclose(Ac[3, 3, 2:5, 2:5], sten, rtol=1e-13, atol=0)
+    assert np.allclose(Ac[7, 7, 6:9, 6:9], sten, rtol=1e-13, atol=0)
 
 
 def test_vcycle_symmetric_and_contracting():
