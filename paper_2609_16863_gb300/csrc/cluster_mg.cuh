@@ -299,6 +299,37 @@ __device__ __forceinline__ void cl_prolong(const ClL<A>& f, const ClL<A>& cv, in
     }
 }
 
+// xh = x_f (buffer kx) + P x_c (buffer kc) into buffer kout for this CTA's rows and its two ghost
+// rows (rows outside the grid stay zero): the first post-smoothing sweep then reads xh without a
+// cluster barrier, because each CTA computes its own ghost rows from its ghost rows of x_f and x_c.
+// With kout == kx every element is read and written by the same thread.
+template <class A>
+__device__ __forceinline__ void cl_prolong_ext(const ClL<A>& f, const ClL<A>& cv, int kx, int kc, int kout, int tid,
+                                               int nthr) {
+    const int n0 = f.n0;
+    const int np = f.nr > 0 ? (f.nr + 2) * n0 : 0;
+    for (int p = tid; p < np; p += nthr) {
+        const int lr = cl_div(p, f.magic) - 1;
+        const int c = p - (lr + 1) * n0;
+        const int F = f.a + lr;
+        if (F < 0 || F >= f.n1) continue;
+        int y0, y1, x0, x1;
+        bool yi, xi;
+        cl_interp(F, y0, y1, yi);
+        cl_interp(c, x0, x1, xi);
+        const A wy = yi ? A(1) : A(0.5), wx = xi ? A(1) : A(0.5);
+        const A w00 = wy * wx, w01 = xi ? A(0) : w00, w10 = yi ? A(0) : w00, w11 = (xi || yi) ? A(0) : w00;
+        const A* r0 = cv.el(kc, y0 - cv.a, 0);
+        const A* r1 = cv.el(kc, y1 - cv.a, 0);
+        A acc = *f.el(kx, lr, c);
+        acc += w00 * r0[x0];
+        acc += w01 * r0[x1];
+        acc += w10 * r1[x0];
+        acc += w11 * r1[x1];
+        *f.el(kout, lr, c) = acc;
+    }
+}
+
 // All mg_cycles V-cycles of (M + c K) x = b for one item, b and x in global memory.
 template <class SI>
 __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* __restrict__ ctx, const int* active,
@@ -320,10 +351,22 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
     const int rank = (int)cl_rank();
     const int L = t.L, T = t.T;
     if (tid == 0) S.rank = rank;
-    // zero every x / b buffer (the padding columns and boundary ghost rows stay zero)
-    {
-        const int end = t.off[L - 1] + 3 * (t.maxr[L - 1] + 2) * (t.g[L - 1].n0 + 2);
-        for (int i = tid; i < end; i += nthr) sm[i] = A(0);
+    // zero the padding columns and ghost rows of every x / b buffer (interiors are written before
+    // they are read; the zeros stand for the Dirichlet boundary)
+    for (int l = 0; l < L; ++l) {
+        const int ld = t.g[l].n0 + 2, rows = t.maxr[l] + 2, xs = rows * ld;
+        const int nrl = l < T ? t.rlo[l][rank + 1] - t.rlo[l][rank] : t.g[l].n1;   // this CTA's rows
+        A* base = sm + t.off[l];
+        const int nedge = 2 * ld + 2 * rows;          // ghost rows -1 and nrl, two padding columns
+        for (int i = tid; i < 3 * nedge; i += nthr) {
+            const int k = i / nedge, e = i - k * nedge;
+            int idx;
+            if (e < ld) idx = e;                                  // ghost row -1
+            else if (e < 2 * ld) idx = (nrl + 1) * ld + e - ld;   // ghost row nrl
+            else if (e < 2 * ld + rows) idx = (e - 2 * ld) * ld;  // column -1
+            else idx = (e - 2 * ld - rows) * ld + ld - 1;         // column n0
+            base[k * xs + idx] = A(0);
+        }
     }
     if (tid < T) {
         const int l = tid;
@@ -479,7 +522,13 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
             }
             int kr;
             if (zero && t.nu1 == 0) {
-                kr = 2;                                   // x = 0: the residual is b
+                // x = 0: the residual is b; clear x (own and ghost rows) for the interpolation later
+                kr = 2;
+                const int nz = f.nr > 0 ? (f.nr + 2) * f.n0 : 0;
+                for (int p = tid; p < nz; p += nthr) {
+                    const int lr = cl_div(p, f.magic) - 1;
+                    *f.el(k, lr, p - (lr + 1) * f.n0) = A(0);
+                }
                 cl_step_sync(dist);                       // b rows were written by this level's restriction
             } else {
                 cl_residual(f, k, tid, nthr);
@@ -535,11 +584,20 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
             const ClL<A> f = cl_level(S, sm, l);
             const ClL<A> cv = cl_level(S, sm, l + 1);
             int k = (cur >> l) & 1u;
-            cl_prolong(f, cv, k, (cur >> (l + 1)) & 1u, tid, nthr);
-            cl_step_sync(dist);
-            for (int sw = 0; sw < t.nu2; ++sw) {
-                cl_sweep(f, k, false, tid, nthr);
-                k ^= 1;
+            const int kc = (cur >> (l + 1)) & 1u;
+            if (t.nu2 > 0) {
+                // x += P x_c in place on own and ghost rows (no remote store: every CTA computes its
+                // ghost rows itself), then the first sweep into the other buffer; a neighbour's
+                // stores of that sweep land in a buffer nobody reads during this step
+                cl_prolong_ext(f, cv, k, kc, k, tid, nthr);
+                __syncthreads();
+                for (int sw = 0; sw < t.nu2; ++sw) {
+                    cl_sweep(f, k, false, tid, nthr);
+                    k ^= 1;
+                    cl_step_sync(dist);
+                }
+            } else {
+                cl_prolong(f, cv, k, kc, tid, nthr);
                 cl_step_sync(dist);
             }
             cur = (cur & ~(1u << l)) | ((unsigned)k << l);

@@ -44,7 +44,10 @@ def kappa_field(ns, seed=3):
 
 SHAPES = [((12, 10), 3, "radau", 2, False), ((9, 9), 4, "radau", 3, False), ((16, 16), 2, "gauss", 2, False),
           ((6, 5, 7), 3, "radau", 3, False), ((11, 13), 3, "radau", 3, True), ((7, 6, 5), 2, "radau", 2, True),
-          ((5, 5), 1, "radau", 1, False), ((1, 1), 2, "radau", 2, False), ((33, 17), 5, "radau", 2, False)]
+          ((5, 5), 1, "radau", 1, False), ((1, 1), 2, "radau", 2, False), ((33, 17), 5, "radau", 2, False),
+          # several multigrid levels (coarsening stops at <= 256 unknowns): 2D shapes take the
+          # cluster-resident V-cycle in the Schur sweep, the 3D one the level kernels
+          ((40, 36), 2, "radau", 2, False), ((34, 37), 2, "radau", 3, True), ((14, 12, 10), 2, "radau", 2, False)]
 
 
 @pytest.mark.parametrize("ns,nt,method,s,var", SHAPES)
@@ -83,6 +86,20 @@ def test_shifted_solve_vcycles(ns, nt, method, s, var):
         x = host(S.shifted_solve(i, to_dev(b), zeros(op.nx)))
         ref = P.mg[i].solve(b, 3)
         assert rel_max(x, ref) <= 1e-12, (i, rel_max(x, ref))
+
+
+@pytest.mark.parametrize("nu1,nu2", [(0, 2), (1, 1), (2, 0), (3, 1), (0, 0), (1, 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_shifted_solve_smoother_counts(nu1, nu2, prec):
+    """Pre/post smoothing counts other than (2, 2): zero guesses without pre-smoothing, no
+    post-smoothing, odd counts (the ping-pong buffer bookkeeping)."""
+    ns = (40, 36)
+    S, op, P = make(ns, 2, "radau", 3, prec=prec, nu1=nu1, nu2=nu2)
+    for i in range(3):
+        b = synth.random_vector(op.nx, 40 + i)
+        x = host(S.shifted_solve(i, to_dev(b), zeros(op.nx)))
+        ref = P.mg[i].solve(b, 3)
+        assert rel_max(x, ref) <= (1e-12 if prec == "fp64" else 2e-5), (i, rel_max(x, ref))
 
 
 @pytest.mark.parametrize("ns,nt,method,s,var", SHAPES)
@@ -138,10 +155,11 @@ def test_solve_fp64_matches_oracle(ns, nt, method, s, var):
     assert info.converged and ref.converged
     assert info.outer_its == ref.outer_its
     assert np.linalg.norm(x - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
-    # both meet the tolerance; the final true residuals are compared only when they are
-    # above the rounding floor of b - A x (~1e-11 here), where they are deterministic
+    # both meet the tolerance; the final true residuals are compared only where they are not
+    # dominated by the rounding floor of b - A x (it grows with ||A|| ||x||, e.g. with kappa):
+    # there the true residual tracks the last Arnoldi estimate and is deterministic
     assert info.rel_res <= 1e-10
-    if ref.rel_res > 1e-11:
+    if ref.history and ref.rel_res <= 2.0 * ref.history[-1]:
         assert abs(info.rel_res - ref.rel_res) <= 1e-2 * ref.rel_res
 
 
