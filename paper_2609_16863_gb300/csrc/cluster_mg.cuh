@@ -35,7 +35,7 @@
 namespace aao {
 
 constexpr int kClMax = 16;            // CTAs per cluster (16 needs the non-portable size)
-constexpr int kClThreads = 1024;
+constexpr int kClThreads = 512;
 
 template <class SI> struct ClCtx {
     using A = typename PT<SI>::A;
@@ -70,38 +70,8 @@ template <class A> struct ClLev {
     A* pd[3];                 // ghost row above the range of the next non-empty CTA
 };
 
-template <class SI> struct ClShared {
-    ClCtx<SI> t;
-    ClLev<typename PT<SI>::A> lv[kMaxLevels];
-    int rank;
-};
-
-__device__ __forceinline__ unsigned cl_rank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ void cl_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// Barrier after a step: the cluster for distributed levels, the CTA for replicated ones.
-__device__ __forceinline__ void cl_step_sync(bool dist) {
-    if (dist) cl_sync();
-    else __syncthreads();
-}
-
-// Generic address of the same shared-memory location in CTA `rank` of the cluster.
-template <class T> __device__ __forceinline__ T* cl_map(T* p, unsigned rank) {
-    unsigned long long out;
-    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(p), "r"(rank));
-    return reinterpret_cast<T*>(out);
-}
-
-__device__ __forceinline__ int cl_div(int p, unsigned magic) { return (int)__umulhi((unsigned)p, magic); }
-
-// One level as a step sees it, held in registers for the step's loop.
+// One level as a step sees it (built once per launch in shared memory; a step copies it to
+// registers only in warps that have points of the level).
 template <class A> struct ClL {
     int n0, n1, nr, a, ld, xs, cs;
     unsigned magic;
@@ -129,6 +99,38 @@ template <class A> struct ClL {
         }
     }
 };
+
+template <class SI> struct ClShared {
+    ClCtx<SI> t;
+    ClLev<typename PT<SI>::A> lv[kMaxLevels];
+    ClL<typename PT<SI>::A> lev[kMaxLevels];
+    int rank;
+};
+
+__device__ __forceinline__ unsigned cl_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cl_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Barrier after a step: the cluster for distributed levels, the CTA for replicated ones.
+__device__ __forceinline__ void cl_step_sync(bool dist) {
+    if (dist) cl_sync();
+    else __syncthreads();
+}
+
+// Generic address of the same shared-memory location in CTA `rank` of the cluster.
+template <class T> __device__ __forceinline__ T* cl_map(T* p, unsigned rank) {
+    unsigned long long out;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(p), "r"(rank));
+    return reinterpret_cast<T*>(out);
+}
+
+__device__ __forceinline__ int cl_div(int p, unsigned magic) { return (int)__umulhi((unsigned)p, magic); }
 
 template <class SI>
 __device__ __forceinline__ ClL<typename PT<SI>::A> cl_level(const ClShared<SI>& S, typename PT<SI>::A* sm, int l) {
@@ -195,7 +197,9 @@ __device__ __forceinline__ A cl_apply(const ClL<A>& v, int p, int lr, int c, con
 
 // Damped Jacobi into buffer 1-kin: zero ? w b : x + w (b - A x), x = buffer kin.
 template <class A>
-__device__ __forceinline__ void cl_sweep(const ClL<A>& v, int kin, bool zero, int tid, int nthr) {
+__device__ __forceinline__ void cl_sweep(const ClL<A>& vin, int kin, bool zero, int tid, int nthr) {
+    if (tid >= vin.nr * vin.n0) return;
+    const ClL<A> v = vin;
     const int n0 = v.n0;
     const int np = v.nr * n0;
     for (int p = tid; p < np; p += nthr) {
@@ -215,7 +219,9 @@ __device__ __forceinline__ void cl_sweep(const ClL<A>& v, int kin, bool zero, in
 
 // Residual b - A x of buffer kin into buffer 1 - kin.
 template <class A>
-__device__ __forceinline__ void cl_residual(const ClL<A>& v, int kin, int tid, int nthr) {
+__device__ __forceinline__ void cl_residual(const ClL<A>& vin, int kin, int tid, int nthr) {
+    if (tid >= vin.nr * vin.n0) return;
+    const ClL<A> v = vin;
     const int n0 = v.n0;
     const int np = v.nr * n0;
     for (int p = tid; p < np; p += nthr) {
@@ -230,8 +236,10 @@ __device__ __forceinline__ void cl_residual(const ClL<A>& v, int kin, int tid, i
 // any_row: the coarse level is the replicated coarsest; fine rows come from rowtab (row i of
 // buffer 0, first interior column, in the CTA that owns it).
 template <class A>
-__device__ __forceinline__ void cl_restrict(const ClL<A>& f, const ClL<A>& cv, int kr, bool any_row,
+__device__ __forceinline__ void cl_restrict(const ClL<A>& fin, const ClL<A>& cvin, int kr, bool any_row,
                                             const A* const* rowtab, int tid, int nthr) {
+    if (tid >= cvin.nr * cvin.n0) return;
+    const ClL<A> f = fin, cv = cvin;
     const int n0c = cv.n0;
     const int np = cv.nr * n0c;
     for (int p = tid; p < np; p += nthr) {
@@ -275,7 +283,9 @@ __device__ __forceinline__ void cl_interp(int F, int& j0, int& j1, bool& inj) {
 
 // x_f (buffer kx) += P x_c (buffer kc) on the fine rows this CTA computes.
 template <class A>
-__device__ __forceinline__ void cl_prolong(const ClL<A>& f, const ClL<A>& cv, int kx, int kc, int tid, int nthr) {
+__device__ __forceinline__ void cl_prolong(const ClL<A>& fin, const ClL<A>& cvin, int kx, int kc, int tid, int nthr) {
+    if (tid >= fin.nr * fin.n0) return;
+    const ClL<A> f = fin, cv = cvin;
     const int n0 = f.n0;
     const int np = f.nr * n0;
     for (int p = tid; p < np; p += nthr) {
@@ -304,8 +314,10 @@ __device__ __forceinline__ void cl_prolong(const ClL<A>& f, const ClL<A>& cv, in
 // cluster barrier, because each CTA computes its own ghost rows from its ghost rows of x_f and x_c.
 // With kout == kx every element is read and written by the same thread.
 template <class A>
-__device__ __forceinline__ void cl_prolong_ext(const ClL<A>& f, const ClL<A>& cv, int kx, int kc, int kout, int tid,
-                                               int nthr) {
+__device__ __forceinline__ void cl_prolong_ext(const ClL<A>& fin, const ClL<A>& cvin, int kx, int kc, int kout,
+                                               int tid, int nthr) {
+    if (fin.nr == 0 || tid >= (fin.nr + 2) * fin.n0) return;
+    const ClL<A> f = fin, cv = cvin;
     const int n0 = f.n0;
     const int np = f.nr > 0 ? (f.nr + 2) * n0 : 0;
     for (int p = tid; p < np; p += nthr) {
@@ -402,6 +414,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
         }
     }
     __syncthreads();
+    if (tid < L) S.lev[tid] = cl_level(S, sm, tid);
     // ---- stage b, faces, stencils, Jacobi weights and this CTA's rows of the coarsest inverse
     // (loads from global memory are issued in groups before the shared-memory stores)
     {
@@ -513,7 +526,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
         // block barriers
         for (int l = 0; l < L - 1; ++l) {
             const bool dist = l < T;
-            const ClL<A> f = cl_level(S, sm, l);
+            const ClL<A>& f = S.lev[l];
             int k = (cur >> l) & 1u;
             for (int sw = 0; sw < t.nu1; ++sw) {
                 cl_sweep(f, k, zero && sw == 0, tid, nthr);
@@ -536,7 +549,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
                 cl_step_sync(dist);
             }
             cur = (cur & ~(1u << l)) | ((unsigned)k << l);
-            const ClL<A> cv = cl_level(S, sm, l + 1);
+            const ClL<A>& cv = S.lev[l + 1];
             cl_restrict(f, cv, kr, dist && l + 1 >= T, rowtab, tid, nthr);
             __syncthreads();
             zero = true;
@@ -545,7 +558,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
         // per row, then the other CTAs' rows gathered after a cluster barrier
         {
             const int l = L - 1;
-            const ClL<A> v = cl_level(S, sm, l);
+            const ClL<A> v = S.lev[l];
             const int nc = v.n0 * v.n1;
             const int k = (cur >> l) & 1u;
             A* bvec = v.X + (1 - k) * v.xs;           // b of the coarsest level, unpadded copy
@@ -581,8 +594,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
         // ---- up
         for (int l = L - 2; l >= 0; --l) {
             const bool dist = l < T;
-            const ClL<A> f = cl_level(S, sm, l);
-            const ClL<A> cv = cl_level(S, sm, l + 1);
+            const ClL<A>& f = S.lev[l];
+            const ClL<A>& cv = S.lev[l + 1];
             int k = (cur >> l) & 1u;
             const int kc = (cur >> (l + 1)) & 1u;
             if (t.nu2 > 0) {
@@ -605,7 +618,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
     }
     // ---- write this CTA's rows of x_0
     {
-        const ClL<A> v = cl_level(S, sm, 0);
+        const ClL<A> v = S.lev[0];
         const int k = cur & 1u;
         if constexpr (PT<SI>::scaled) {
             const int w = tid >> 5, lane = tid & 31, nw = nthr >> 5;

@@ -589,29 +589,37 @@ static __global__ void k_dense_level(FineDesc fd, double* Adense) {
 }
 
 // In-place Gauss--Jordan inverse (SPD input, no pivoting needed), one block.
-static __global__ void k_gauss_jordan(double* A, double* Inv, int n, int* fail) {
+static __global__ void __launch_bounds__(1024) k_gauss_jordan(double* A, double* Inv, int n, int* fail) {
     pdl_prologue();
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Inv[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+    // one CTA; warps take rows, lanes take columns; the scaled pivot rows live in shared memory
+    __shared__ double prow[kMaxCoarsest], pinvrow[kMaxCoarsest];
+    __shared__ double piv;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = w; i < n; i += nw)
+        for (int j = lane; j < n; j += 32) Inv[i * n + j] = i == j ? 1.0 : 0.0;
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-        __shared__ double piv;
         if (threadIdx.x == 0) {
             piv = A[k * n + k];
             if (!(piv > 0.0)) *fail = 1;
         }
         __syncthreads();
-        double pinv = 1.0 / piv;
+        const double pinv = 1.0 / piv;
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            A[k * n + j] *= pinv;
-            Inv[k * n + j] *= pinv;
+            const double a = A[k * n + j] * pinv, v = Inv[k * n + j] * pinv;
+            A[k * n + j] = a;
+            Inv[k * n + j] = v;
+            prow[j] = a;
+            pinvrow[j] = v;
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-            int i = idx / n, j = idx % n;
+        for (int i = w; i < n; i += nw) {
             if (i == k) continue;
-            double f = A[i * n + k];
-            if (j != k) A[i * n + j] -= f * A[k * n + j];
-            Inv[i * n + j] -= f * Inv[k * n + j];
+            const double f = A[i * n + k];
+            for (int j = lane; j < n; j += 32) {
+                if (j != k) A[i * n + j] -= f * prow[j];
+                Inv[i * n + j] -= f * pinvrow[j];
+            }
         }
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x)

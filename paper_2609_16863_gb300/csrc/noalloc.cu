@@ -173,7 +173,7 @@ extern "C" aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double 
         fd.sten = sten[l];
     }
     launch(k_dense_level, (unsigned)((nc + 127) / 128), 128, 0, st, fd, dense);
-    launch(k_gauss_jordan, 1, 256, 0, st, dense, dinv, nc, fail);
+    launch(k_gauss_jordan, 1, 1024, 0, st, dense, dinv, nc, fail);
     AAO_LAUNCH_CHECK();
     LevelOp<double> ops[kMaxLevels];
     for (int l = 0; l < L; ++l) {

@@ -244,7 +244,7 @@ class Precond : public PrecondBase {
                 cd.sten = sten64[L - 1];
             }
             launch(k_dense_level, (unsigned)((ncst + 127) / 128), 128, 0, st(), cd, dense);
-            launch(k_gauss_jordan, 1, 256, 0, st(), dense, dinv64, ncst, fail);
+            launch(k_gauss_jordan, 1, 1024, 0, st(), dense, dinv64, ncst, fail);
             AAO_LAUNCH_CHECK();
             AAO_TRY(ar.alloc(&Dinv[i], (size_t)ncst * ncst));
             launch(k_convert_dense<A>, (unsigned)(((long long)ncst * ncst + 255) / 256), 256, 0, st(), 
