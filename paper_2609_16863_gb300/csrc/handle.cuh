@@ -116,7 +116,11 @@ struct Handle {
     // reduction blocks per item: about 8 blocks per SM over the whole batch, at
     // most one 32-column segment per warp
     int nchunk_for(int B, long long segments) const {
-        long long target = (152LL * 8 + B - 1) / B;
+        // a single small item (the Schur sweep's inner solves): one block per SM, so fewer
+        // partials and atomics on the item's counter; otherwise about eight blocks per SM in total
+        // (enough loads in flight for the long outer vectors)
+        const bool small_single = B == 1 && segments < 152LL * kWarpsPerBlock * 32;
+        long long target = small_single ? 152LL : (152LL * 8 + B - 1) / B;
         long long maxc = (segments + kWarpsPerBlock - 1) / kWarpsPerBlock;
         long long c = target < maxc ? target : maxc;
         if (c > red_cap_chunks) c = red_cap_chunks;
