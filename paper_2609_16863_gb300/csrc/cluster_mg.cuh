@@ -30,6 +30,8 @@
 // vectors stay on chip in the arithmetic type.
 #pragma once
 
+#include <type_traits>
+
 #include "mg.cuh"
 
 namespace aao {
@@ -342,6 +344,85 @@ __device__ __forceinline__ void cl_prolong_ext(const ClL<A>& fin, const ClL<A>& 
     }
 }
 
+// Asynchronous copy of 4 bytes global -> shared (no register round trip).
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+// Staging for FP32 storage: every copy (b with ghost rows, faces, this CTA's stencil rows and rows
+// of the coarsest inverse) is issued asynchronously before one wait; the Jacobi weights follow
+// from the staged data.  Same values as the register path.
+template <class SI>
+__device__ __forceinline__ void cl_stage_async(const ClCtx<SI>& t, int rank, int L, int T, float* sm, const Vec<SI>& bv,
+                                               int tid, int nthr) {
+    const Geo& g = t.g[0];
+    const int a = t.rlo[0][rank], nr = t.rlo[0][rank + 1] - a;
+    const int ld0 = g.n0 + 2, xs0 = (t.maxr[0] + 2) * ld0;
+    float* B0 = sm + t.off[0] + 2 * xs0;
+    const float* bsrc = reinterpret_cast<const float*>(bv.d);
+    if (nr > 0) {
+        const int nb0 = (nr + 2) * g.n0;
+        for (int p = tid; p < nb0; p += nthr) {
+            const int lr = cl_div(p, t.magic[0]) - 1;
+            const int row = a + lr, c = p - (lr + 1) * g.n0;
+            if (row >= 0 && row < g.n1) cp_async4(B0 + (lr + 1) * ld0 + c + 1, bsrc + (long long)row * g.n0 + c);
+            else B0[(lr + 1) * ld0 + c + 1] = 0.f;
+        }
+    }
+    const int w = g.n0 + 1;
+    if (t.fine0 && t.has_faces) {
+        const int nfx = nr * w, nfy = (nr + 1) * g.n0;
+        const float* fx = reinterpret_cast<const float*>(t.fx) + (long long)a * w;
+        const float* fy = reinterpret_cast<const float*>(t.fy) + (long long)a * g.n0;
+        for (int p = tid; p < nfx; p += nthr) cp_async4(sm + t.fxoff + p, fx + p);
+        for (int p = tid; p < nfy; p += nthr) cp_async4(sm + t.fyoff + p, fy + p);
+    }
+    for (int l = t.fine0 ? 1 : 0; l < L - 1; ++l) {
+        const Geo& gl = t.g[l];
+        const bool dist = l < T;
+        const int al = dist ? t.rlo[l][rank] : 0;
+        const int npl = dist ? (t.rlo[l][rank + 1] - al) * gl.n0 : (int)gl.nx;
+        const int cs = t.maxr[l] * gl.n0;
+        const float* src = reinterpret_cast<const float*>(t.sten[l]) + (long long)al * gl.n0;
+        for (int q = 0; q < 9; ++q)
+            for (int p = tid; p < npl; p += nthr) cp_async4(sm + t.soff[l] + q * cs + p, src + (long long)q * gl.nx + p);
+    }
+    {
+        const int nc = (int)t.g[L - 1].nx;
+        const int n = (t.cs[rank + 1] - t.cs[rank]) * nc;
+        const float* src = reinterpret_cast<const float*>(t.Dinv) + (long long)t.cs[rank] * nc;
+        for (int p = tid; p < n; p += nthr) cp_async4(sm + t.dinv_off + p, src + p);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    // Jacobi weights omega / a_PP from the staged faces / stencil centres
+    if (t.fine0) {
+        const int np0 = nr * g.n0;
+        for (int p = tid; p < np0; p += nthr) {
+            float kd;
+            if (t.has_faces) {
+                const int lr = cl_div(p, t.magic[0]);
+                const int c = p - lr * g.n0;
+                const float* fxr = sm + t.fxoff + lr * w;
+                const float* fyr = sm + t.fyoff + lr * g.n0;
+                kd = fxr[c] + fxr[c + 1] + fyr[c] + fyr[c + g.n0];
+            } else {
+                kd = 2.f * (float)g.hx2 + 2.f * (float)g.hy2;
+            }
+            sm[t.woff[0] + p] = t.omega / (t.sigma + t.c * kd);
+        }
+    }
+    for (int l = t.fine0 ? 1 : 0; l < L - 1; ++l) {
+        const Geo& gl = t.g[l];
+        const bool dist = l < T;
+        const int al = dist ? t.rlo[l][rank] : 0;
+        const int npl = dist ? (t.rlo[l][rank + 1] - al) * gl.n0 : (int)gl.nx;
+        const int cs = t.maxr[l] * gl.n0;
+        for (int p = tid; p < npl; p += nthr) sm[t.woff[l] + p] = t.omega / sm[t.soff[l] + 4 * cs + p];
+    }
+}
+
 // All mg_cycles V-cycles of (M + c K) x = b for one item, b and x in global memory.
 template <class SI>
 __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* __restrict__ ctx, const int* active,
@@ -415,105 +496,109 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
     }
     __syncthreads();
     if (tid < L) S.lev[tid] = cl_level(S, sm, tid);
-    // ---- stage b, faces, stencils, Jacobi weights and this CTA's rows of the coarsest inverse
-    // (loads from global memory are issued in groups before the shared-memory stores)
-    {
-        constexpr int U = 4;
-        const Geo& g = t.g[0];
-        const int a = t.rlo[0][rank], nr = t.rlo[0][rank + 1] - a;
-        const int np0 = nr * g.n0, ld0 = g.n0 + 2, xs0 = (t.maxr[0] + 2) * ld0;
-        View<SI> bs = view_of(bv, 0, 0, g.n0);
-        A* B0 = sm + t.off[0] + 2 * xs0;
-        // rows a-1 .. a+nr of b (the ghost rows too: the residual of a zero guess is b)
-        const int nb0 = nr > 0 ? (nr + 2) * g.n0 : 0;
-        for (int p0 = tid; p0 < nb0; p0 += U * nthr) {
-            A v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int p = p0 + u * nthr;
-                const int lr = cl_div(p, t.magic[0]) - 1;
-                const int row = a + lr;
-                v[u] = p < nb0 && row >= 0 && row < g.n1 ? bs.at(row, p - (lr + 1) * g.n0) : A(0);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int p = p0 + u * nthr;
-                const int lr = cl_div(p, t.magic[0]) - 1;
-                if (p < nb0) B0[(lr + 1) * ld0 + p - (lr + 1) * g.n0 + 1] = v[u];
-            }
-        }
-        if (t.fine0) {
-            const int w = g.n0 + 1;
-            if (t.has_faces) {
-                const int nfx = nr * w, nfy = (nr + 1) * g.n0;
-                const A* fx = t.fx + (long long)a * w;
-                const A* fy = t.fy + (long long)a * g.n0;
-                for (int p0 = tid; p0 < nfx; p0 += U * nthr) {
-                    A v[U];
-#pragma unroll
-                    for (int u = 0; u < U; ++u) v[u] = p0 + u * nthr < nfx ? fx[p0 + u * nthr] : A(0);
-#pragma unroll
-                    for (int u = 0; u < U; ++u)
-                        if (p0 + u * nthr < nfx) sm[t.fxoff + p0 + u * nthr] = v[u];
-                }
-                for (int p0 = tid; p0 < nfy; p0 += U * nthr) {
-                    A v[U];
-#pragma unroll
-                    for (int u = 0; u < U; ++u) v[u] = p0 + u * nthr < nfy ? fy[p0 + u * nthr] : A(0);
-#pragma unroll
-                    for (int u = 0; u < U; ++u)
-                        if (p0 + u * nthr < nfy) sm[t.fyoff + p0 + u * nthr] = v[u];
-                }
-            }
-            for (int p0 = tid; p0 < np0; p0 += U * nthr) {
-                A kd[U];
-#pragma unroll
+    if constexpr (std::is_same<SI, float>::value && std::is_same<typename PT<SI>::A, float>::value) {
+        cl_stage_async(t, rank, L, T, sm, bv, tid, nthr);
+    } else {
+        // ---- stage b, faces, stencils, Jacobi weights and this CTA's rows of the coarsest inverse
+        // (loads from global memory are issued in groups before the shared-memory stores)
+        {
+            constexpr int U = 4;
+            const Geo& g = t.g[0];
+            const int a = t.rlo[0][rank], nr = t.rlo[0][rank + 1] - a;
+            const int np0 = nr * g.n0, ld0 = g.n0 + 2, xs0 = (t.maxr[0] + 2) * ld0;
+            View<SI> bs = view_of(bv, 0, 0, g.n0);
+            A* B0 = sm + t.off[0] + 2 * xs0;
+            // rows a-1 .. a+nr of b (the ghost rows too: the residual of a zero guess is b)
+            const int nb0 = nr > 0 ? (nr + 2) * g.n0 : 0;
+            for (int p0 = tid; p0 < nb0; p0 += U * nthr) {
+                A v[U];
+    #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int p = p0 + u * nthr;
-                    const int lr = cl_div(p, t.magic[0]);
-                    const int c = p - lr * g.n0;
-                    if (t.has_faces && p < np0) {
-                        const long long fxi = (long long)(a + lr) * w + c, fyi = (long long)(a + lr) * g.n0 + c;
-                        kd[u] = t.fx[fxi] + t.fx[fxi + 1] + t.fy[fyi] + t.fy[fyi + g.n0];
-                    } else {
-                        kd[u] = A(2) * A(g.hx2) + A(2) * A(g.hy2);
+                    const int lr = cl_div(p, t.magic[0]) - 1;
+                    const int row = a + lr;
+                    v[u] = p < nb0 && row >= 0 && row < g.n1 ? bs.at(row, p - (lr + 1) * g.n0) : A(0);
+                }
+    #pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int p = p0 + u * nthr;
+                    const int lr = cl_div(p, t.magic[0]) - 1;
+                    if (p < nb0) B0[(lr + 1) * ld0 + p - (lr + 1) * g.n0 + 1] = v[u];
+                }
+            }
+            if (t.fine0) {
+                const int w = g.n0 + 1;
+                if (t.has_faces) {
+                    const int nfx = nr * w, nfy = (nr + 1) * g.n0;
+                    const A* fx = t.fx + (long long)a * w;
+                    const A* fy = t.fy + (long long)a * g.n0;
+                    for (int p0 = tid; p0 < nfx; p0 += U * nthr) {
+                        A v[U];
+    #pragma unroll
+                        for (int u = 0; u < U; ++u) v[u] = p0 + u * nthr < nfx ? fx[p0 + u * nthr] : A(0);
+    #pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            if (p0 + u * nthr < nfx) sm[t.fxoff + p0 + u * nthr] = v[u];
+                    }
+                    for (int p0 = tid; p0 < nfy; p0 += U * nthr) {
+                        A v[U];
+    #pragma unroll
+                        for (int u = 0; u < U; ++u) v[u] = p0 + u * nthr < nfy ? fy[p0 + u * nthr] : A(0);
+    #pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            if (p0 + u * nthr < nfy) sm[t.fyoff + p0 + u * nthr] = v[u];
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (p0 + u * nthr < np0) sm[t.woff[0] + p0 + u * nthr] = t.omega / (t.sigma + t.c * kd[u]);
-            }
-        }
-        for (int l = t.fine0 ? 1 : 0; l < L - 1; ++l) {
-            const Geo& gl = t.g[l];
-            const bool dist = l < T;
-            const int al = dist ? t.rlo[l][rank] : 0;
-            const int npl = dist ? (t.rlo[l][rank + 1] - al) * gl.n0 : (int)gl.nx;
-            const int cs = t.maxr[l] * gl.n0;
-            const SI* src = t.sten[l] + (long long)al * gl.n0;
-            for (int p = tid; p < npl; p += nthr) {
-                A v[9];
-#pragma unroll
-                for (int q = 0; q < 9; ++q) v[q] = PT<SI>::ld(src[(long long)q * gl.nx + p]);
-#pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    if constexpr (PT<SI>::scaled) v[q] *= t.sten_sc[l][q];
-                    sm[t.soff[l] + q * cs + p] = v[q];
+                for (int p0 = tid; p0 < np0; p0 += U * nthr) {
+                    A kd[U];
+    #pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int p = p0 + u * nthr;
+                        const int lr = cl_div(p, t.magic[0]);
+                        const int c = p - lr * g.n0;
+                        if (t.has_faces && p < np0) {
+                            const long long fxi = (long long)(a + lr) * w + c, fyi = (long long)(a + lr) * g.n0 + c;
+                            kd[u] = t.fx[fxi] + t.fx[fxi + 1] + t.fy[fyi] + t.fy[fyi + g.n0];
+                        } else {
+                            kd[u] = A(2) * A(g.hx2) + A(2) * A(g.hy2);
+                        }
+                    }
+    #pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (p0 + u * nthr < np0) sm[t.woff[0] + p0 + u * nthr] = t.omega / (t.sigma + t.c * kd[u]);
                 }
-                sm[t.woff[l] + p] = t.omega / v[4];
             }
-        }
-        {
-            const int nc = (int)t.g[L - 1].nx;
-            const int n = (t.cs[rank + 1] - t.cs[rank]) * nc;
-            const A* src = t.Dinv + (long long)t.cs[rank] * nc;
-            for (int p0 = tid; p0 < n; p0 += U * nthr) {
-                A v[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) v[u] = p0 + u * nthr < n ? src[p0 + u * nthr] : A(0);
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (p0 + u * nthr < n) sm[t.dinv_off + p0 + u * nthr] = v[u];
+            for (int l = t.fine0 ? 1 : 0; l < L - 1; ++l) {
+                const Geo& gl = t.g[l];
+                const bool dist = l < T;
+                const int al = dist ? t.rlo[l][rank] : 0;
+                const int npl = dist ? (t.rlo[l][rank + 1] - al) * gl.n0 : (int)gl.nx;
+                const int cs = t.maxr[l] * gl.n0;
+                const SI* src = t.sten[l] + (long long)al * gl.n0;
+                for (int p = tid; p < npl; p += nthr) {
+                    A v[9];
+    #pragma unroll
+                    for (int q = 0; q < 9; ++q) v[q] = PT<SI>::ld(src[(long long)q * gl.nx + p]);
+    #pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        if constexpr (PT<SI>::scaled) v[q] *= t.sten_sc[l][q];
+                        sm[t.soff[l] + q * cs + p] = v[q];
+                    }
+                    sm[t.woff[l] + p] = t.omega / v[4];
+                }
+            }
+            {
+                const int nc = (int)t.g[L - 1].nx;
+                const int n = (t.cs[rank + 1] - t.cs[rank]) * nc;
+                const A* src = t.Dinv + (long long)t.cs[rank] * nc;
+                for (int p0 = tid; p0 < n; p0 += U * nthr) {
+                    A v[U];
+    #pragma unroll
+                    for (int u = 0; u < U; ++u) v[u] = p0 + u * nthr < n ? src[p0 + u * nthr] : A(0);
+    #pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (p0 + u * nthr < n) sm[t.dinv_off + p0 + u * nthr] = v[u];
+                }
             }
         }
     }
