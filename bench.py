@@ -36,6 +36,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-8 residual, mixed vs FP64 precond, same GB300; precond HBM GB/s"
 WORKLOAD = "fd2d_n256_radau3_nt128"
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_cluster_mg launch (single-item 256x256
+# shifted solve, FP32 storage, 512-thread CTAs), from one ncu capture of the current kernel; the
+# kernel's inputs are L2-resident, so this is far below its algorithmic bytes
+CLUSTER_MG_DRAM_BYTES = 1364
 
 
 def parse():
@@ -381,6 +385,9 @@ def main():
     rows, tot = profiled(lambda: S.solve(f, u0, x))
     roof = roof_of(rows[0], tot)
     roof["measured"] = "CUDA events around each launch during one extra (eager) solve"
+    if "k_cluster_mg" in roof["kernel"] and args.prec == "fp32" and args.workload == WORKLOAD and not args.small:
+        roof["traffic"] = CLUSTER_MG_DRAM_BYTES
+        roof["limit"] = "latency: 25 cluster barriers and dependent step chains per V-cycle on 16 SMs"
     top = [{"kernel": r["kernel"], "launches": r["launches"], "ms": round(r["ms"], 3),
             "GB/s": round(r["bytes"] / (r["ms"] * 1e-3) / 1e9, 1) if r["ms"] > 0 else 0.0} for r in rows[:8]]
     # the batched Theta_tilde phase alone (all nt time blocks at once): HBM-bound kernels
