@@ -221,8 +221,72 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_resid_restrict(LevelOp<S> op,
     });
 }
 
+// Level kinds known at compile time (fewer registers than the run-time dispatch of level_apply):
+// 0 any, 1 matrix-free FD level, 2 stored 9-point (2D), 3 stored 27-point (3D),
+// 4: matrix-free FD level in 2D.
+inline int level_kind(int fine, int d) { return fine ? (d == 2 ? 4 : 1) : (d == 2 ? 2 : 3); }
+
+template <int KIND, class S, class SU>
+__device__ __forceinline__ void level_apply_k(const LevelOp<S>& op, const View<SU>& u, long long row, int j, int k,
+                                              int c, typename PT<S>::A& Au, typename PT<S>::A& diag) {
+    using A = typename PT<S>::A;
+    const Geo& g = op.g;
+    if constexpr (KIND == 1) {
+        Au = op.sigma * A(u.at(row, c)) + op.c * A(fd_K(u, g, op.faces, row, j, k, c));
+        diag = op.sigma + op.c * fd_K_diag<A>(g, op.faces, row, j, k, c);
+    } else if constexpr (KIND == 4) {
+        // fd_K / fd_K_diag for d = 2 (same arithmetic, 32-bit indexing within the item)
+        const int r = (int)row, n0 = g.n0;
+        const A uP = A(u.at(r, c));
+        const A uW = c > 0 ? A(u.at(r, c - 1)) : A(0);
+        const A uE = c + 1 < n0 ? A(u.at(r, c + 1)) : A(0);
+        const A uS = j > 0 ? A(u.at(r - 1, c)) : A(0);
+        const A uN = j + 1 < g.n1 ? A(u.at(r + 1, c)) : A(0);
+        A K, kd;
+        if (op.faces.fx == nullptr) {
+            K = A(g.hx2) * (A(2) * uP - uW - uE) + A(g.hy2) * (A(2) * uP - uS - uN);
+            kd = A(2) * A(g.hx2) + A(2) * A(g.hy2);
+        } else {
+            const int fxi = r * (n0 + 1) + c, fyi = j * n0 + c;
+            const A fx0 = A(op.faces.fx[fxi]), fx1 = A(op.faces.fx[fxi + 1]);
+            const A fy0 = A(op.faces.fy[fyi]), fy1 = A(op.faces.fy[fyi + n0]);
+            K = fx0 * (uP - uW) + fx1 * (uP - uE) + fy0 * (uP - uS) + fy1 * (uP - uN);
+            kd = fx0 + fx1 + fy0 + fy1;
+        }
+        Au = op.sigma * uP + op.c * K;
+        diag = op.sigma + op.c * kd;
+    } else if constexpr (KIND == 2) {
+        const long long p = row * g.n0 + c;
+        A acc = A(0);
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int jj = j + dy;
+            if (jj < 0 || jj >= g.n1) continue;
+            const long long rr = row + dy;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int cc = c + dx;
+                if (cc < 0 || cc >= g.n0) continue;
+                acc += sten_coef(op, (dx + 1) + 3 * (dy + 1), p) * A(u.at(rr, cc));
+            }
+        }
+        Au = acc;
+        diag = sten_coef(op, 4, p);
+    } else {
+        level_apply(op, u, row, j, k, c, Au, diag);
+    }
+}
+
+template <int KIND, class S>
+__device__ __forceinline__ typename PT<S>::A level_diag_k(const LevelOp<S>& op, long long row, int j, int k, int c) {
+    using A = typename PT<S>::A;
+    if constexpr (KIND == 1 || KIND == 4) return op.sigma + op.c * fd_K_diag<A>(op.g, op.faces, row, j, k, c);
+    else if constexpr (KIND == 2) return sten_coef(op, 4, row * op.g.n0 + c);
+    else return level_diag(op, row, j, k, c);
+}
+
 // x_out = x_in + omega D^{-1} (b - A x_in); x_in.d == nullptr means x_in = 0.
-template <class S>
+template <class S, int KIND = 0>
 __global__ void __launch_bounds__(kPtMaxThreads) k_smooth(LevelOp<S> op, PtMap pm, int B, const int* active, Vec<S> xin,
                                                  Vec<S> bv, Vec<S> xout, typename PT<S>::A omega) {
     pdl_prologue();
@@ -240,23 +304,21 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_smooth(LevelOp<S> op, PtMap p
     row_store_ptrs(xout, q.b, 0, row, g.n0, out, osc);
     if (xin.d == nullptr) {
         pt_store<S>(out, osc, pm, q.c0, q.valid, [&](int c) -> A {
-            A dg;
-            if (op.fine) dg = op.sigma + op.c * fd_K_diag<A>(g, op.faces, row, j, k, c);
-            else dg = sten_coef(op, g.d == 3 ? 13 : 4, row * g.n0 + c);
+            const A dg = level_diag_k<KIND>(op, row, j, k, c);
             return omega * bb.at(row, c) / dg;
         });
     } else {
         View<S> xx = view_of(xin, q.b, 0, g.n0);
         pt_store<S>(out, osc, pm, q.c0, q.valid, [&](int c) -> A {
             A Au, dg;
-            level_apply(op, xx, row, j, k, c, Au, dg);
+            level_apply_k<KIND>(op, xx, row, j, k, c, Au, dg);
             return xx.at(row, c) + omega * (bb.at(row, c) - Au) / dg;
         });
     }
 }
 
 // r = b - A x
-template <class S>
+template <class S, int KIND = 0>
 __global__ void __launch_bounds__(kPtMaxThreads) k_residual(LevelOp<S> op, PtMap pm, int B, const int* active, Vec<S> xv,
                                                    Vec<S> bv, Vec<S> rv) {
     pdl_prologue();
@@ -275,7 +337,7 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_residual(LevelOp<S> op, PtMap
     row_store_ptrs(rv, q.b, 0, row, g.n0, out, osc);
     pt_store<S>(out, osc, pm, q.c0, q.valid, [&](int c) -> A {
         A Au, dg;
-        level_apply(op, xx, row, j, k, c, Au, dg);
+        level_apply_k<KIND>(op, xx, row, j, k, c, Au, dg);
         return bb.at(row, c) - Au;
     });
 }

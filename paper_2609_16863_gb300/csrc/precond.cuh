@@ -563,6 +563,18 @@ class Precond : public PrecondBase {
         return v;
     }
 
+    // Smoother and residual launches specialised by level kind (2D matrix-free, 2D stored; 3D generic).
+    template <class... Args> void launch_smooth(int kind, dim3 grid, dim3 block, Args... args) {
+        if (kind == 4) launch(k_smooth<SI, 4>, grid, block, 0, st(), args...);
+        else if (kind == 2) launch(k_smooth<SI, 2>, grid, block, 0, st(), args...);
+        else launch(k_smooth<SI, 0>, grid, block, 0, st(), args...);
+    }
+    template <class... Args> void launch_residual(int kind, dim3 grid, dim3 block, Args... args) {
+        if (kind == 4) launch(k_residual<SI, 4>, grid, block, 0, st(), args...);
+        else if (kind == 2) launch(k_residual<SI, 2>, grid, block, 0, st(), args...);
+        else launch(k_residual<SI, 0>, grid, block, 0, st(), args...);
+    }
+
     // x_out = V-cycle(l) applied to (x_in, b); x_in.d == nullptr: zero guess.
     aao_status vcycle(int l, int stage, int B, const int* act, Vec<SI> xin, Vec<SI> b, Vec<SI> xout) {
         const Geo& g = lev[l].g;
@@ -620,7 +632,7 @@ class Precond : public PrecondBase {
         for (; q < nu1; ++q) {
             Vec<SI> d = dest();
             bytes_hint((cur.d ? 3.0 : 2.0) * nact * g.nx * sizeof(SI));
-            launch(k_smooth<SI>, pbl, pth, 0, st(), op, pm, B, act, cur, b, d, om);
+            launch_smooth(level_kind(op.fine, g.d), pbl, pth, op, pm, B, act, cur, b, d, om);
             cur = d;
         }
         // residual and restriction
@@ -632,7 +644,7 @@ class Precond : public PrecondBase {
             launch(k_restrict<SI>, cbl, cth, 0, st(), g, gc, pmc, B, act, b, lev[l + 1].Bb);
         } else {
             bytes_hint(3.0 * nact * g.nx * sizeof(SI));
-            launch(k_residual<SI>, pbl, pth, 0, st(), op, pm, B, act, cur, b, lev[l].Rr);
+            launch_residual(level_kind(op.fine, g.d), pbl, pth, op, pm, B, act, cur, b, lev[l].Rr);
             bytes_hint(1.0 * nact * (g.nx + gc.nx) * sizeof(SI));
             launch(k_restrict<SI>, cbl, cth, 0, st(), g, gc, pmc, B, act, lev[l].Rr, lev[l + 1].Bb);
         }
@@ -655,7 +667,7 @@ class Precond : public PrecondBase {
         for (; q < nu2; ++q) {
             Vec<SI> d = dest();
             bytes_hint(3.0 * nact * g.nx * sizeof(SI));
-            launch(k_smooth<SI>, pbl, pth, 0, st(), op, pm, B, act, cur, b, d, om);
+            launch_smooth(level_kind(op.fine, g.d), pbl, pth, op, pm, B, act, cur, b, d, om);
             cur = d;
         }
         AAO_LAUNCH_CHECK();
