@@ -131,7 +131,8 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_scale_store(PtMap pm, int row
     }
     const int n0 = pm.n0;
     const SR* x = src + (long long)q.b * sbs + q.row * n0;
-    A inv = (denom && q.valid) ? A(1.0 / denom[(long long)q.b * dstride]) : A(1);
+    // the reciprocal in the arithmetic type: an FP64 division per thread is slow on this GPU
+    A inv = (denom && q.valid) ? A(1) / A(denom[(long long)q.b * dstride]) : A(1);
     SO* o; float* osc;
     row_store_ptrs(out, q.b, 0, q.row, n0, o, osc);
     pt_store<SO>(o, osc, pm, q.c0, q.valid, [&](int c) -> A { return A(x[c]) * inv; });
@@ -316,6 +317,35 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_rana_rhs(Geo g, PtMap pm, int
     View<SV> v = view_of(V, q.b, (long long)stage * g.nx, g.n0);
     SZ* o; float* osc;
     row_store_ptrs(out, q.b, 0, row, g.n0, o, osc);
+    if (g.d == 2 && !sop.q1) {
+        // fd_K for d = 2 with 32-bit indexing within the item (same arithmetic)
+        const int r = (int)row, n0 = g.n0;
+        pt_store<SZ>(o, osc, pm, q.c0, q.valid, [&](int c) -> A {
+            A acc = (A)v.at(row, c);
+            for (int jj = 0; jj < s; ++jj) {
+                const double cf = coef[jj];
+                if (cf != 0.0) {
+                    View<SZ> zj = view_of(Z, q.b, (long long)jj * g.nx, n0);
+                    const A uP = zj.at(r, c);
+                    const A uW = c > 0 ? zj.at(r, c - 1) : A(0);
+                    const A uE = c + 1 < n0 ? zj.at(r, c + 1) : A(0);
+                    const A uS = j > 0 ? zj.at(r - 1, c) : A(0);
+                    const A uN = j + 1 < g.n1 ? zj.at(r + 1, c) : A(0);
+                    A K;
+                    if (sop.faces.fx == nullptr) {
+                        K = A(g.hx2) * (A(2) * uP - uW - uE) + A(g.hy2) * (A(2) * uP - uS - uN);
+                    } else {
+                        const int fxi = r * (n0 + 1) + c, fyi = j * n0 + c;
+                        K = A(sop.faces.fx[fxi]) * (uP - uW) + A(sop.faces.fx[fxi + 1]) * (uP - uE) +
+                            A(sop.faces.fy[fyi]) * (uP - uS) + A(sop.faces.fy[fyi + n0]) * (uP - uN);
+                    }
+                    acc -= tau * (A)cf * K;
+                }
+            }
+            return acc;
+        });
+        return;
+    }
     pt_store<SZ>(o, osc, pm, q.c0, q.valid, [&](int c) -> A {
         A acc = (A)v.at(row, c);
         for (int jj = 0; jj < s; ++jj) {
