@@ -317,6 +317,47 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_smooth(LevelOp<S> op, PtMap p
     }
 }
 
+// k_smooth for unscaled storage with RPT rows per thread (rows r0, r0 + rpc, ...): all rows'
+// values are computed before any store, so their loads are in flight together; fewer, longer CTAs
+// for large batches.  One column per thread (n0 <= n0p).
+template <class S, int KIND, int RPT>
+__global__ void __launch_bounds__(kPtMaxThreads) k_smooth_rows(LevelOp<S> op, PtMap pm, int B, const int* active,
+                                                               Vec<S> xin, Vec<S> bv, Vec<S> xout,
+                                                               typename PT<S>::A omega) {
+    pdl_prologue();
+    using A = typename PT<S>::A;
+    static_assert(!PT<S>::scaled, "unscaled storage only");
+    const Geo g = op.g;
+    const int b = blockIdx.y;
+    if (b >= B || (active && !active[b])) return;
+    const int c = threadIdx.x;
+    if (c >= g.n0) return;
+    const int r0 = blockIdx.x * pm.rpc * RPT + threadIdx.y;
+    View<S> bb = view_of(bv, b, 0, g.n0);
+    S* out = xout.d + (long long)b * xout.bs;
+    A v[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int row = r0 + i * pm.rpc;
+        v[i] = A(0);
+        if (row < g.R) {
+            if (xin.d == nullptr) {
+                v[i] = omega * bb.at(row, c) / level_diag_k<KIND>(op, row, row, 0, c);
+            } else {
+                View<S> xx = view_of(xin, b, 0, g.n0);
+                A Au, dg;
+                level_apply_k<KIND>(op, xx, row, row, 0, c, Au, dg);
+                v[i] = xx.at(row, c) + omega * (bb.at(row, c) - Au) / dg;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int row = r0 + i * pm.rpc;
+        if (row < g.R) out[(long long)row * g.n0 + c] = PT<S>::st(v[i]);
+    }
+}
+
 // r = b - A x
 template <class S, int KIND = 0>
 __global__ void __launch_bounds__(kPtMaxThreads) k_residual(LevelOp<S> op, PtMap pm, int B, const int* active, Vec<S> xv,

@@ -565,6 +565,16 @@ class Precond : public PrecondBase {
 
     // Smoother and residual launches specialised by level kind (2D matrix-free, 2D stored; 3D generic).
     template <class... Args> void launch_smooth(int kind, dim3 grid, dim3 block, Args... args) {
+        if constexpr (!PT<SI>::scaled) {
+            // large 2D batches: four rows per thread (grid.y = items)
+            constexpr int kRows = 4;
+            if ((kind == 4 || kind == 2) && grid.y >= 16) {
+                dim3 gr((grid.x + kRows - 1) / kRows, grid.y);
+                if (kind == 4) launch(k_smooth_rows<SI, 4, kRows>, gr, block, 0, st(), args...);
+                else launch(k_smooth_rows<SI, 2, kRows>, gr, block, 0, st(), args...);
+                return;
+            }
+        }
         if (kind == 4) launch(k_smooth<SI, 4>, grid, block, 0, st(), args...);
         else if (kind == 2) launch(k_smooth<SI, 2>, grid, block, 0, st(), args...);
         else launch(k_smooth<SI, 0>, grid, block, 0, st(), args...);

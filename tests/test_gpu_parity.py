@@ -142,6 +142,18 @@ def test_precond_apply(ns, nt, method, s, var):
     assert rel_max(zt, P.apply_T(r)) <= 1e-11
 
 
+@pytest.mark.parametrize("ns,var", [((40, 36), False), ((34, 37), True)])
+def test_precond_apply_many_blocks(ns, var):
+    """16+ time blocks: the batched Theta_tilde phase takes its large-batch kernels."""
+    kap = kappa_field(ns) if var else None
+    S, op, P = make(ns, 18, "radau", 2, kappa=kap)
+    r = synth.random_vector(op.n_st, 77)
+    z = host(S.precond_apply(to_dev(r), zeros(op.n_st)))
+    assert rel_max(z, P.apply(r)) <= 1e-11
+    zt = host(S.precond_apply(to_dev(r), zeros(op.n_st), transpose=True))
+    assert rel_max(zt, P.apply_T(r)) <= 1e-11
+
+
 @pytest.mark.parametrize("ns,nt,method,s,var", SHAPES)
 def test_solve_fp64_matches_oracle(ns, nt, method, s, var):
     kap = kappa_field(ns) if var else None
