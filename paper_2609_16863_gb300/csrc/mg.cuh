@@ -358,6 +358,40 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_smooth_rows(LevelOp<S> op, Pt
     }
 }
 
+// r = b - A x for unscaled storage, RPT rows per thread (as k_smooth_rows).
+template <class S, int KIND, int RPT>
+__global__ void __launch_bounds__(kPtMaxThreads) k_residual_rows(LevelOp<S> op, PtMap pm, int B, const int* active,
+                                                                 Vec<S> xv, Vec<S> bv, Vec<S> rv) {
+    pdl_prologue();
+    using A = typename PT<S>::A;
+    static_assert(!PT<S>::scaled, "unscaled storage only");
+    const Geo g = op.g;
+    const int b = blockIdx.y;
+    if (b >= B || (active && !active[b])) return;
+    const int c = threadIdx.x;
+    if (c >= g.n0) return;
+    const int r0 = blockIdx.x * pm.rpc * RPT + threadIdx.y;
+    View<S> xx = view_of(xv, b, 0, g.n0);
+    View<S> bb = view_of(bv, b, 0, g.n0);
+    S* out = rv.d + (long long)b * rv.bs;
+    A v[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int row = r0 + i * pm.rpc;
+        v[i] = A(0);
+        if (row < g.R) {
+            A Au, dg;
+            level_apply_k<KIND>(op, xx, row, row, 0, c, Au, dg);
+            v[i] = bb.at(row, c) - Au;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int row = r0 + i * pm.rpc;
+        if (row < g.R) out[(long long)row * g.n0 + c] = PT<S>::st(v[i]);
+    }
+}
+
 // r = b - A x
 template <class S, int KIND = 0>
 __global__ void __launch_bounds__(kPtMaxThreads) k_residual(LevelOp<S> op, PtMap pm, int B, const int* active, Vec<S> xv,
@@ -474,6 +508,49 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_prolong_add(Geo gf, Geo gc, P
             }
         return acc;
     });
+}
+
+// k_prolong_add in 2D for unscaled storage, RPT rows per thread (as k_smooth_rows).
+template <class S, int RPT>
+__global__ void __launch_bounds__(kPtMaxThreads) k_prolong_add_rows(Geo gf, Geo gc, PtMap pm, int B, const int* active,
+                                                                    Vec<S> xcv, Vec<S> xin, Vec<S> xout) {
+    pdl_prologue();
+    using A = typename PT<S>::A;
+    static_assert(!PT<S>::scaled, "unscaled storage only");
+    const int b = blockIdx.y;
+    if (b >= B || (active && !active[b])) return;
+    const int c = threadIdx.x;
+    if (c >= gf.n0) return;
+    const int r0 = blockIdx.x * pm.rpc * RPT + threadIdx.y;
+    View<S> xc = view_of(xcv, b, 0, gc.n0);
+    const bool has_in = xin.d != nullptr;
+    View<S> xi = has_in ? view_of(xin, b, 0, gf.n0) : View<S>{nullptr, nullptr, gf.n0};
+    S* out = xout.d + (long long)b * xout.bs;
+    int Jx[2];
+    float wx[2];
+    const int mx = interp_1d(c, gc.n0, Jx, wx);
+    A v[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int row = r0 + i * pm.rpc;
+        v[i] = A(0);
+        if (row < gf.R) {
+            int Jy[2];
+            float wy[2];
+            const int my = interp_1d(row, gc.n1, Jy, wy);
+            A acc = has_in ? xi.at(row, c) : A(0);
+            for (int bq = 0; bq < my; ++bq) {
+                const A wyz = A(wy[bq]) * A(1.f);
+                for (int e = 0; e < mx; ++e) acc += wyz * A(wx[e]) * xc.at(Jy[bq], Jx[e]);
+            }
+            v[i] = acc;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int row = r0 + i * pm.rpc;
+        if (row < gf.R) out[(long long)row * gf.n0 + c] = PT<S>::st(v[i]);
+    }
 }
 
 // x_out = xp + omega D^{-1} (b - A xp) with xp = x_in + P xc computed on the fly at

@@ -580,6 +580,15 @@ class Precond : public PrecondBase {
         else launch(k_smooth<SI, 0>, grid, block, 0, st(), args...);
     }
     template <class... Args> void launch_residual(int kind, dim3 grid, dim3 block, Args... args) {
+        if constexpr (!PT<SI>::scaled) {
+            constexpr int kRows = 4;
+            if ((kind == 4 || kind == 2) && grid.y >= 16) {
+                dim3 gr((grid.x + kRows - 1) / kRows, grid.y);
+                if (kind == 4) launch(k_residual_rows<SI, 4, kRows>, gr, block, 0, st(), args...);
+                else launch(k_residual_rows<SI, 2, kRows>, gr, block, 0, st(), args...);
+                return;
+            }
+        }
         if (kind == 4) launch(k_residual<SI, 4>, grid, block, 0, st(), args...);
         else if (kind == 2) launch(k_residual<SI, 2>, grid, block, 0, st(), args...);
         else launch(k_residual<SI, 0>, grid, block, 0, st(), args...);
@@ -671,7 +680,15 @@ class Precond : public PrecondBase {
         } else {
             Vec<SI> d = dest();
             bytes_hint(1.0 * nact * (gc.nx + (cur.d ? 2.0 : 1.0) * g.nx) * sizeof(SI));
-            launch(k_prolong_add<SI>, pbl, pth, 0, st(), g, gc, pm, B, act, lev[l + 1].X, cur, d);
+            bool rows_done = false;
+            if constexpr (!PT<SI>::scaled) {
+                if (g.d == 2 && B >= 16) {
+                    launch(k_prolong_add_rows<SI, 4>, dim3((pbl.x + 3) / 4, pbl.y), pth, 0, st(), g, gc, pm, B, act,
+                           lev[l + 1].X, cur, d);
+                    rows_done = true;
+                }
+            }
+            if (!rows_done) launch(k_prolong_add<SI>, pbl, pth, 0, st(), g, gc, pm, B, act, lev[l + 1].X, cur, d);
             cur = d;
         }
         for (; q < nu2; ++q) {
