@@ -418,6 +418,11 @@ class Precond : public PrecondBase {
                 o += (n + 3) / 4 * 4;
                 return (int)at;
             };
+            // Every CTA must own at least one row of every distributed level: a CTA whose coarse
+            // range is empty would interpolate from coarse ghost rows that no neighbour stores to
+            // (neighbours push only to non-empty CTAs).  Grids with few rows for their width
+            // (e.g. 120 x 17 at C = 16) fail this and take a smaller cluster or the level kernels.
+            bool nonempty = true;
             for (int l = 0; l < L; ++l) {
                 const Geo& gl = lev[l].g;
                 t.g[l] = gl;
@@ -426,13 +431,17 @@ class Precond : public PrecondBase {
                     for (int r = 0; r <= C; ++r)
                         t.rlo[l][r] = l == 0 ? (int)((long long)r * gl.n1 / C) : t.rlo[l - 1][r] / 2;
                     int mr = 0;
-                    for (int r = 0; r < C; ++r) mr = std::max(mr, t.rlo[l][r + 1] - t.rlo[l][r]);
+                    for (int r = 0; r < C; ++r) {
+                        mr = std::max(mr, t.rlo[l][r + 1] - t.rlo[l][r]);
+                        nonempty = nonempty && t.rlo[l][r + 1] > t.rlo[l][r];
+                    }
                     t.maxr[l] = std::max(mr, 1);
                 } else {
                     t.maxr[l] = gl.n1;
                 }
                 t.off[l] = take(3LL * (t.maxr[l] + 2) * (gl.n0 + 2));
             }
+            if (!nonempty) continue;
             for (int l = 0; l < L; ++l) {
                 t.soff[l] = t.woff[l] = -1;
                 if ((l >= 1 || !fine0) && l < L - 1) t.soff[l] = take(9LL * t.maxr[l] * lev[l].g.n0);

@@ -102,6 +102,24 @@ def test_shifted_solve_smoother_counts(nu1, nu2, prec):
         assert rel_max(x, ref) <= (1e-12 if prec == "fp64" else 2e-5), (i, rel_max(x, ref))
 
 
+@pytest.mark.parametrize("ns,var,prec", [((120, 17), False, "fp64"), ((120, 17), True, "fp64"),
+                                         ((120, 17), False, "fp32"), ((100, 12), False, "fp64"),
+                                         ((100, 12), False, "fp32")])
+@pytest.mark.parametrize("nu1,nu2", [(2, 2), (0, 1)])
+def test_shifted_solve_anisotropic(ns, var, prec, nu1, nu2):
+    """Short, wide grids: 120 x 17 leaves a 16-CTA cluster with CTAs that own no row of a coarse
+    level, so the plan takes 8 CTAs; 100 x 12 takes the level kernels.  FP32 bound: the unit
+    square on these grids has h_x much smaller than h_y, and the oracle's V-cycle repeated in
+    float32 arithmetic already differs from FP64 by up to 3e-5 (relative, max norm)."""
+    kap = kappa_field(ns) if var else None
+    S, op, P = make(ns, 2, "radau", 2, kappa=kap, prec=prec, nu1=nu1, nu2=nu2)
+    for i in range(2):
+        b = synth.random_vector(op.nx, 60 + i)
+        x = host(S.shifted_solve(i, to_dev(b), zeros(op.nx)))
+        ref = P.mg[i].solve(b, 3)
+        assert rel_max(x, ref) <= (1e-12 if prec == "fp64" else 2e-4), (i, rel_max(x, ref))
+
+
 @pytest.mark.parametrize("ns,nt,method,s,var", SHAPES)
 def test_pint_apply(ns, nt, method, s, var):
     kap = kappa_field(ns) if var else None
