@@ -952,6 +952,7 @@ aao_status aao_rk_solve_batched(int nprob, const aao_rk_handle* hs, const double
             set_error("null handle in batch");
             return AAO_ERR_ARG;
         }
+    if (nprob == 0) return AAO_OK;
     int dev = 0;
     AAO_CUDA_TRY(cudaGetDevice(&dev));
     // one host thread per problem: every problem's FGMRES loop (and its

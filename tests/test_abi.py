@@ -68,3 +68,127 @@ def test_setup_rejects_bad_arguments_without_gpu(lib):
     o.prec_P, o.prec_Pint = 1, 0          # FP32 P with FP64 P_int is not a supported pair
     st = L.aao_rk_setup(ctypes.byref(g), 0.1, 4, ctypes.byref(t), ctypes.byref(o), ctypes.byref(h))
     assert st == -1
+
+
+def _valid_setup_args():
+    from paper_2609_16863_gb300 import _lib
+    L = _lib.load()
+    g = _lib.aao_grid()
+    g.dim = 2
+    g.n[0] = g.n[1] = 8
+    g.n[2] = 1
+    g.len[0] = g.len[1] = g.len[2] = 1.0
+    g.disc = 0
+    t = _lib.aao_tableau()
+    t.s = 2
+    o = _lib.aao_options()
+    L.aao_rk_default_options(ctypes.byref(o))
+    return L, g, t, o
+
+
+def _set(obj, field, value):
+    if "[" in field:
+        name, idx = field[:-1].split("[")
+        getattr(obj, name)[int(idx)] = value
+    else:
+        setattr(obj, field, value)
+
+
+# (what to change, value, words expected in the error message); every case fails in argument
+# validation, before any device call
+SETUP_BAD = [
+    ("grid.dim", 1, b"dim"), ("grid.dim", 4, b"dim"), ("grid.n[1]", 0, b"grid sizes"),
+    ("grid.len[0]", -1.0, b"grid sizes"), ("grid.len[1]", float("nan"), b"grid sizes"),
+    ("grid.disc", 7, b"discretisation"), ("q1_kappa", None, b"kappa"),
+    ("tau", 0.0, b"tau"), ("tau", float("nan"), b"tau"), ("nt", 0, b"tau"),
+    ("tab.s", 0, b"stages"), ("tab.s", 9, b"stages"),
+    ("opts.restart", 0, b"restart"), ("opts.restart", 65, b"restart"), ("opts.maxit", -1, b"restart"),
+    ("opts.tol", float("nan"), b"restart"), ("opts.tol", -1.0, b"restart"),
+    ("opts.inner_maxit", 17, b"inner_maxit"), ("opts.mg_cycles", 0, b"mg_cycles"),
+    ("opts.mg_pre", -1, b"mg_pre"), ("opts.mg_post", -1, b"mg_pre"), ("opts.mg_omega", 0.0, b"mg_omega"),
+    ("opts.prec_P", 7, b"precision"), ("fp64_fp32", None, b"FP64"), ("bf16_fp32", None, b"16-bit"),
+    ("fp16_bf16", None, b"16-bit"), ("null_grid", None, b"null"), ("null_out", None, b"null output"),
+]
+
+
+@pytest.mark.parametrize("what,value,words", SETUP_BAD)
+def test_setup_validation_table(lib, what, value, words):
+    L, g, t, o = _valid_setup_args()
+    tau, nt = 0.1, 4
+    gp, out = ctypes.byref(g), ctypes.c_void_p()
+    outp = ctypes.byref(out)
+    if what == "q1_kappa":
+        g.disc = 1
+        g.kappa = 0x1000                  # never dereferenced: rejected first
+    elif what == "fp64_fp32":
+        o.prec_P, o.prec_Pint = 0, 1
+    elif what == "bf16_fp32":
+        o.prec_P, o.prec_Pint = 2, 1
+    elif what == "fp16_bf16":
+        o.prec_P, o.prec_Pint = 3, 2
+    elif what == "null_grid":
+        gp = None
+    elif what == "null_out":
+        outp = None
+    elif what == "tau":
+        tau = value
+    elif what == "nt":
+        nt = value
+    else:
+        obj, field = what.split(".", 1)
+        _set({"grid": g, "tab": t, "opts": o}[obj], field, value)
+    st = L.aao_rk_setup(gp, tau, nt, ctypes.byref(t), ctypes.byref(o), outp)
+    assert st == -1
+    assert not out.value
+    assert words in L.aao_rk_last_error(), L.aao_rk_last_error()
+
+
+NOALLOC_BAD = [
+    ("null_grid", b"null"), ("dim", b"dim"), ("kappa", b"constant-coefficient"), ("q1", b"constant-coefficient"),
+    ("c", b"c >= 0"), ("cycles", b"cycles"), ("pre", b"pre/post"), ("omega", b"omega"),
+    ("size0", b"positive"), ("too_large", b"65536"),
+]
+
+
+@pytest.mark.parametrize("what,words", NOALLOC_BAD)
+def test_noalloc_validation_table(lib, what, words):
+    L, g, _, _ = _valid_setup_args()
+    args = dict(c=0.01, cycles=3, pre=2, post=2, omega=0.8)
+    gp = ctypes.byref(g)
+    if what == "null_grid":
+        gp = None
+    elif what == "dim":
+        g.dim = 1
+    elif what == "kappa":
+        g.kappa = 0x1000
+    elif what == "q1":
+        g.disc = 1
+    elif what == "c":
+        args["c"] = -1.0
+    elif what == "cycles":
+        args["cycles"] = 0
+    elif what == "pre":
+        args["pre"] = -1
+    elif what == "omega":
+        args["omega"] = float("nan")
+    elif what == "size0":
+        g.n[0] = 0
+    elif what == "too_large":
+        g.n[0], g.n[1] = 300, 300
+    dummy = ctypes.c_void_p(0x1000)       # never dereferenced: rejected first
+    st = L.aao_rk_shifted_solve_noalloc(gp, ctypes.c_double(args["c"]), args["cycles"], args["pre"], args["post"],
+                                        ctypes.c_double(args["omega"]), dummy, dummy, None)
+    assert st == -1
+    assert words in L.aao_rk_last_error(), L.aao_rk_last_error()
+
+
+def test_batched_validation(lib):
+    from paper_2609_16863_gb300 import _lib
+    L = _lib.load()
+    assert L.aao_rk_solve_batched(0, None, None, None, None, None) == 0     # empty batch: no device work
+    assert L.aao_rk_solve_batched(-1, None, None, None, None, None) == -1
+    assert L.aao_rk_solve_batched(1, None, None, None, None, None) == -1
+    hs = (ctypes.c_void_p * 1)(None)
+    vec = (ctypes.c_void_p * 1)(0x1000)
+    assert L.aao_rk_solve_batched(1, hs, vec, vec, vec, None) == -1
+    assert b"null handle" in L.aao_rk_last_error()
