@@ -19,6 +19,8 @@ It is a plain, slow, obviously-correct restatement of the method:
                     for Theta_tilde, the Schur approximation S_tilde of
                     Eq. (AppSchur), the block-triangular P_tilde of Eq. (AppPrec),
                     and their transposes.
+* ``mgrit``      -- two-level multigrid reduction in time for S_tilde's time
+                    recurrence (the parallel implementation of Sec. 5).
 * ``fgmres``     -- restarted right-preconditioned flexible GMRES (Algorithm 1
                     with P_L = I, P_R = P_tilde).
 * ``sequential`` -- sequential RK time stepping with direct stage solves.

@@ -31,6 +31,11 @@ then z_V = Theta_tilde^{-T} (r_V - Psi_1^T z_v), (Psi_1^T z_v)_{n,i} = -tau b_i 
 Theta_tilde^{-T} is inner GMRES on Theta_hat^T right-preconditioned by P_int^T
 (a backward stage sweep).
 
+With schur="mgrit" the time recurrences of S_tilde and S_tilde^T are solved
+approximately by two-level MGRIT (module mgrit), as in the paper's parallel
+implementation (Sec. 5); the fine step is the substitution step above, the
+coarse step the same with step size m tau.
+
 Parity: pinned by the exact-inverse limit (Theta_tilde = Theta_hat, exact
 M^{-1}: FGMRES converges in <= 2 iterations, Sec. 3) and, for P_int, by the
 s = 1 limit and a dense block-triangular solve (tests).
@@ -41,6 +46,8 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
+from . import mgrit
+from .aao import AllAtOnce
 from .multigrid import Hierarchy
 from .tableau import ldu
 from .operators import q1_jacobi_interval
@@ -107,7 +114,8 @@ class Preconditioner:
     """
 
     def __init__(self, op, ns, inner_maxit=3, inner_tol=1e-3, mg_cycles=3, nu1=2, nu2=2,
-                 omega=2.0 / 3.0, cheb_steps=20, exact=False):
+                 omega=2.0 / 3.0, cheb_steps=20, exact=False, schur="sequential", mgrit_m=8,
+                 mgrit_iters=1, mgrit_relax="FCF"):
         self.op = op
         self.ns = tuple(ns)
         self.s, self.nt, self.nx = op.s, op.nt, op.nx
@@ -129,6 +137,20 @@ class Preconditioner:
         else:
             self.mg = [Hierarchy(A, self.ns, omega, nu1, nu2) for A in self.shifted]
         self.inner_its = 0
+        # S_tilde's time recurrence: forward substitution (Eq. AppSchur) or, as in the paper's
+        # parallel implementation (Sec. 5), MGRIT with the same step on the fine level and the
+        # step of size m tau (nt / m steps) on the coarse level
+        if schur not in ("sequential", "mgrit"):
+            raise ValueError("schur is 'sequential' or 'mgrit'")
+        self.schur = schur
+        self.mgrit_m, self.mgrit_iters, self.mgrit_relax = int(mgrit_m), int(mgrit_iters), mgrit_relax
+        self.coarse = None
+        if schur == "mgrit":
+            if self.mgrit_m < 1 or self.nt % self.mgrit_m != 0:
+                raise ValueError("the MGRIT coarsening factor must divide nt")
+            op_c = AllAtOnce(op.K, op.M, self.mgrit_m * op.tau, self.nt // self.mgrit_m, op.A, op.b, op.c)
+            self.coarse = Preconditioner(op_c, ns, inner_maxit, inner_tol, mg_cycles, nu1, nu2, omega,
+                                         cheb_steps, exact)
 
     # -- spatial pieces -------------------------------------------------------
     def shifted_solve(self, i, r):
@@ -222,6 +244,10 @@ class Preconditioner:
                 acc = acc + b[i] * zV[n, i]
             g[n + 1] = rv[n + 1] + tau * op.Mmul(acc)
         w = np.stack([self.mass_inverse(g[n]) for n in range(nt + 1)])
+        if self.schur == "mgrit":
+            zv = mgrit.two_level(self.schur_step, self.coarse.schur_step, w, self.mgrit_m,
+                                 self.mgrit_iters, self.mgrit_relax)
+            return op.join(zv, zV)
         zv = np.empty_like(rv)
         zv[0] = w[0]
         for n in range(nt):
@@ -233,20 +259,44 @@ class Preconditioner:
             zv[n + 1] = acc
         return op.join(zv, zV)
 
+    def schur_step(self, z):
+        """One step of S_tilde's recurrence without its source: z - tau (b^T (x) I)
+        Theta_tilde^{-1} (e (x) K z)."""
+        q = self.inner_solve(np.tile(self.op.K @ z, self.s)).reshape(self.s, self.nx)
+        acc = z.copy()
+        for i in range(self.s):
+            acc = acc - self.op.tau * self.op.b[i] * q[i]
+        return acc
+
+    def schur_step_T(self, u):
+        """One step of S_tilde^T's backward recurrence without its source: u - tau (e^T (x) K^T)
+        Theta_tilde^{-T} (b (x) u)."""
+        q = self.inner_solve(np.concatenate([self.op.b[i] * u for i in range(self.s)]),
+                             transpose=True).reshape(self.s, self.nx)
+        acc = np.zeros(self.nx)
+        for i in range(self.s):
+            acc = acc + self.op.K.T @ q[i]
+        return u - self.op.tau * acc
+
     def apply_T(self, r):
         """z = P_tilde^{-T} r."""
         op = self.op
         rv, rV = op.split(np.asarray(r, dtype=np.float64))
         nt, s, nx, tau, b = self.nt, self.s, self.nx, op.tau, op.b
-        u = np.empty_like(rv)
-        u[nt] = rv[nt]
-        for n in range(nt - 1, -1, -1):
-            t = np.concatenate([b[i] * u[n + 1] for i in range(s)])
-            q = self.inner_solve(t, transpose=True).reshape(s, nx)
-            acc = np.zeros(nx)
-            for i in range(s):
-                acc = acc + op.K.T @ q[i]
-            u[n] = rv[n] + u[n + 1] - tau * acc
+        if self.schur == "mgrit":
+            # the backward recurrence is a forward one in reversed time
+            u = mgrit.two_level(self.schur_step_T, self.coarse.schur_step_T, rv[::-1], self.mgrit_m,
+                                self.mgrit_iters, self.mgrit_relax)[::-1]
+        else:
+            u = np.empty_like(rv)
+            u[nt] = rv[nt]
+            for n in range(nt - 1, -1, -1):
+                t = np.concatenate([b[i] * u[n + 1] for i in range(s)])
+                q = self.inner_solve(t, transpose=True).reshape(s, nx)
+                acc = np.zeros(nx)
+                for i in range(s):
+                    acc = acc + op.K.T @ q[i]
+                u[n] = rv[n] + u[n + 1] - tau * acc
         zv = np.stack([self.mass_inverse_T(u[n]) for n in range(nt + 1)])
         zV = np.empty_like(rV)
         for n in range(nt):
