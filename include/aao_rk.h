@@ -114,7 +114,8 @@ void aao_rk_default_options(aao_options* opts);
 
 /* Build a handle for one problem: operators, Rana shifts tau d_i from the
  * LDU of A_RK (Sec. 3), one multigrid hierarchy per shift with Galerkin
- * coarse stencils, and all workspace.  Returns AAO_ERR_ARG on bad sizes,
+ * coarse stencils, and all workspace.  nt is at most 65534 (time blocks are a
+ * launch grid dimension).  Returns AAO_ERR_ARG on bad sizes,
  * AAO_ERR_BREAKDOWN on a non-positive LDU pivot, AAO_ERR_OOM when the
  * workspace does not fit. */
 aao_status aao_rk_setup(const aao_grid* grid, double tau, int nt, const aao_tableau* tab,

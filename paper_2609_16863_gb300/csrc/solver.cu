@@ -219,6 +219,11 @@ static aao_status validate(const aao_grid* grid, double tau, int nt, const aao_t
         set_error("tau must be > 0 and nt >= 1");
         return AAO_ERR_ARG;
     }
+    if (nt > kMaxNt) {
+        // batched launches put the time blocks (up to nt + 1) in the grid's y dimension
+        set_error("nt must be at most 65534 (time blocks are a launch grid dimension)");
+        return AAO_ERR_ARG;
+    }
     if (tab->s < 1 || tab->s > kMaxS) {
         set_error("tableau stages must be in 1..8");
         return AAO_ERR_ARG;

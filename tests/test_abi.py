@@ -100,7 +100,7 @@ SETUP_BAD = [
     ("grid.dim", 1, b"dim"), ("grid.dim", 4, b"dim"), ("grid.n[1]", 0, b"grid sizes"),
     ("grid.len[0]", -1.0, b"grid sizes"), ("grid.len[1]", float("nan"), b"grid sizes"),
     ("grid.disc", 7, b"discretisation"), ("q1_kappa", None, b"kappa"),
-    ("tau", 0.0, b"tau"), ("tau", float("nan"), b"tau"), ("nt", 0, b"tau"),
+    ("tau", 0.0, b"tau"), ("tau", float("nan"), b"tau"), ("nt", 0, b"tau"), ("nt", 65535, b"65534"),
     ("tab.s", 0, b"stages"), ("tab.s", 9, b"stages"),
     ("opts.restart", 0, b"restart"), ("opts.restart", 65, b"restart"), ("opts.maxit", -1, b"restart"),
     ("opts.tol", float("nan"), b"restart"), ("opts.tol", -1.0, b"restart"),
