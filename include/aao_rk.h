@@ -192,9 +192,10 @@ aao_status aao_rk_grad_kappa(aao_rk_handle h, const double* lambda, const double
 /* Solve nprob independent problems (each with its own handle, possibly of a
  * different grid, nt and s) in one call.  f[p], u0[p], x[p] as in
  * aao_rk_solve (device memory); infos may be NULL.  Returns the first
- * non-OK status, after every problem has been attempted.  nprob == 0 is a
- * no-op returning AAO_OK; nprob < 0, NULL arrays or a NULL handle give
- * AAO_ERR_ARG before any device work. */
+ * non-OK status, after every problem has been attempted.  Problems run on up
+ * to 64 host threads, largest (space-time unknowns) first; each handle may
+ * appear once.  nprob == 0 is a no-op returning AAO_OK; nprob < 0, NULL
+ * arrays, a NULL or repeated handle give AAO_ERR_ARG before any device work. */
 aao_status aao_rk_solve_batched(int nprob, const aao_rk_handle* hs, const double* const* f,
                                 const double* const* u0, double* const* x, aao_info* infos);
 

@@ -24,6 +24,7 @@ constexpr int kMaxRowLen = kWarp * kMaxV;
 constexpr int kMaxInner = 16;            // inner GMRES iterations
 constexpr int kMaxRestart = 64;          // outer FGMRES restart
 constexpr int kMaxNt = 65534;            // time steps: nt + 1 items fit the 65535 grid.y limit
+constexpr int kMaxBatchThreads = 64;     // host workers of a batched solve
 constexpr int kMaxLevels = 16;
 constexpr int kMaxCoarsest = 512;        // unknowns of the dense coarsest solve
 constexpr int kCoarsestTarget = 256;     // coarsening stops at the first level with at most this many unknowns

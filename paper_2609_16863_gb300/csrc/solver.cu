@@ -1,5 +1,6 @@
 // Handle set-up, the FP64 outer FGMRES (Algorithm 1 with P_L = I, P_R =
 // P_tilde, restarted) and the extern "C" entry points of include/aao_rk.h.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -957,24 +958,49 @@ aao_status aao_rk_solve_batched(int nprob, const aao_rk_handle* hs, const double
             set_error("null handle in batch");
             return AAO_ERR_ARG;
         }
+    {
+        // a handle is not thread-safe: each may appear once
+        std::vector<const void*> seen(hs, hs + nprob);
+        std::sort(seen.begin(), seen.end());
+        if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) {
+            set_error("a handle appears more than once in the batch");
+            return AAO_ERR_ARG;
+        }
+    }
     if (nprob == 0) return AAO_OK;
     int dev = 0;
     AAO_CUDA_TRY(cudaGetDevice(&dev));
-    // one host thread per problem: every problem's FGMRES loop (and its
-    // per-iteration convergence test) runs independently, so the GPU overlaps
-    // the latency-bound Schur sweeps of different problems.  Problems whose
-    // handles share a stream serialise on that stream.
+    // Host worker threads, one per problem up to kMaxBatchThreads: every
+    // problem's FGMRES loop (and its per-iteration convergence test) runs
+    // independently, so the GPU overlaps the latency-bound Schur sweeps of
+    // different problems.  Workers take problems largest first (space-time
+    // unknowns), so a long problem does not start last.  Problems whose handles
+    // share a stream serialise on that stream.
+    std::vector<int> order(nprob);
+    for (int p = 0; p < nprob; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->h.nst > hs[b]->h.nst; });
     std::vector<aao_status> st(nprob, AAO_OK);
     std::vector<std::string> err(nprob);
-    std::vector<std::thread> th;
-    th.reserve(nprob);
-    for (int p = 0; p < nprob; ++p) {
-        th.emplace_back([&, p]() {
-            cudaSetDevice(dev);
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        cudaSetDevice(dev);
+        for (int q = next++; q < nprob; q = next++) {
+            const int p = order[q];
             st[p] = aao_rk_solve(hs[p], f[p], 0, u0[p], x[p], 0, infos ? &infos[p] : nullptr);
             if (st[p] != AAO_OK) err[p] = get_error();
-        });
+        }
+    };
+    std::vector<std::thread> th;
+    const int nworkers = std::min(nprob, kMaxBatchThreads);
+    th.reserve(nworkers);
+    for (int w = 0; w < nworkers; ++w) {
+        try {
+            th.emplace_back(work);
+        } catch (const std::exception&) {
+            break;   // fewer workers: the ones running take the remaining problems
+        }
     }
+    if (th.empty()) work();   // no thread could be created: solve on the caller's thread
     for (auto& t : th) t.join();
     for (int p = 0; p < nprob; ++p)
         if (st[p] != AAO_OK) {

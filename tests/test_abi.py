@@ -192,3 +192,13 @@ def test_batched_validation(lib):
     vec = (ctypes.c_void_p * 1)(0x1000)
     assert L.aao_rk_solve_batched(1, hs, vec, vec, vec, None) == -1
     assert b"null handle" in L.aao_rk_last_error()
+
+
+def test_batched_rejects_a_repeated_handle(lib):
+    """Handles are not thread-safe; a batch may not name one twice (checked before any device call)."""
+    from paper_2609_16863_gb300 import _lib
+    L = _lib.load()
+    hs = (ctypes.c_void_p * 3)(0x1000, 0x2000, 0x1000)     # never dereferenced: rejected first
+    vec = (ctypes.c_void_p * 3)(0x3000, 0x3000, 0x3000)
+    assert L.aao_rk_solve_batched(3, hs, vec, vec, vec, None) == -1
+    assert b"more than once" in L.aao_rk_last_error()
