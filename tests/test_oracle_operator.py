@@ -32,6 +32,19 @@ def test_dof_counts_table2():
         assert dof_count(nx_q2, _nt_rule(l, s, 3), s) == dof_q2
 
 
+def test_dof_counts_parallel_cases():
+    """The parallel test cases' printed DoF: n_x (1 + n_t (s + 1)) less one, for all three cases
+    (an off-by-one in the printed counts; Table 2's counts match the formula exactly)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "parallel_dof.txt")
+    rows = [list(map(int, ln.split())) for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for case, s, nx, nt, printed in rows:
+        assert dof_count(nx, nt, s) == printed + 1, case
+        # the operator's own layout count, per spatial unknown
+        one = AllAtOnce(sp.identity(1, format="csr"), None, 1.0, nt, np.eye(s), np.ones(s) / s, np.ones(s))
+        assert one.n_st * nx == dof_count(nx, nt, s)
+
+
 def test_nst_matches_dof_count():
     op = build((5, 4), 1.0, 3, "radau", 3)
     assert op.n_st == dof_count(20, 3, 3)
