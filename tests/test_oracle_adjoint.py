@@ -53,3 +53,25 @@ def test_adjoint_fgmres_matches_dense_transpose_solve():
     lam, its, rr, ok = adjoint_solve(op, ns, g, tol=1e-13, inner_maxit=5, inner_tol=1e-6, omega=0.8)
     ref = np.linalg.solve(op.dense().T, g)
     assert ok and np.linalg.norm(lam - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("disc,ns,nt,s", [("fd", (5, 4), 3, 3), ("fd", (3, 3, 2), 2, 2), ("q1", (4, 5), 3, 2)])
+def test_sequential_adjoint_matches_dense_transpose(disc, ns, nt, s):
+    from oracle.sequential import sequential_adjoint_rk
+    kap = _setup(ns, nt, s, seed=5)[0] if disc == "fd" else None
+    op = build(ns, 0.5, nt, "radau", s, disc=disc, kappa=kap)
+    g = synth.random_vector(op.n_st, 9)
+    ref = np.linalg.solve(op.dense().T, g)
+    assert np.linalg.norm(sequential_adjoint_rk(op, g) - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_adjoint_fgmres_matches_backward_adjoint_rk_at_scale():
+    """Beyond dense sizes: 40 x 36 with a kappa field, Radau IIA s = 3, 16 steps."""
+    from oracle.sequential import sequential_adjoint_rk
+    ns, nt, s = (40, 36), 16, 3
+    kap = np.exp(synth.gaussian_random_field(ns, 0.15, 0.5, synth.rng_for(3, "kappa"), with_boundary=True))
+    op = build(ns, 1.0, nt, "radau", s, kappa=kap)
+    g = synth.random_vector(op.n_st, 11)
+    lam, its, rr, ok = adjoint_solve(op, ns, g, tol=1e-12, inner_maxit=5, inner_tol=1e-6, omega=0.8)
+    ref = sequential_adjoint_rk(op, g)
+    assert ok and np.linalg.norm(lam - ref) <= 1e-10 * np.linalg.norm(ref)
