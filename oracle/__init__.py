@@ -25,8 +25,9 @@ It is a plain, slow, obviously-correct restatement of the method:
                     with P_L = I, P_R = P_tilde).
 * ``sequential`` -- sequential RK time stepping with direct stage solves.
 * ``adjoint``    -- the adjoint solve and gradients of the tracking functional.
-* ``lowprec``    -- round-to-nearest-even storage emulation (bf16/fp16/fp32)
-                    with per-row power-of-two scaling.
 
-Parity status per function is stated in each module header.
+Parity status per function is stated in each module header.  There is no
+low-precision emulation here: the GPU path's FP32/BF16/FP16 storage is
+compared with these FP64 results at tolerances set by the storage precision's
+unit roundoff.
 """
