@@ -15,6 +15,10 @@ residual, at most 100 iterations).  With b the right-hand side:
   then x <- x + Z_k y_k and the true residual is recomputed;
   the solve has converged when the TRUE residual satisfies
   ||b - A x|| <= tol ||b||.
+
+Pins (tests): solutions against dense LU of the assembled operator (2D/3D,
+s = 1..3, Radau and Gauss); the exact-inverse preconditioner converging in
+two iterations (minimal polynomial of degree 2, Sec. 3).
 """
 from __future__ import annotations
 

@@ -16,6 +16,12 @@ mass matrix (Eq. discretized_system_stages).  Two discretisations:
 
 Layout: lexicographic with x fastest; Kronecker products therefore list the
 slowest axis first (kron(Ay, Ax) in 2D).
+
+Pins (tests): K with kappa == 1 against the Kronecker sum of 1D second
+differences; the flux form by symmetry, constant-kappa scaling and its energy
+u^T K u summed face by face;
+Q1 mass row sums and the Jacobi interval of D^{-1} M; the sine eigenpairs of K
+through the closed-form solution.
 """
 from __future__ import annotations
 
