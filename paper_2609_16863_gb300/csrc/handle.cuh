@@ -2,7 +2,10 @@
 // preconditioner implementations.
 #pragma once
 
+#include <cstdlib>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
 #include "krylov.cuh"
@@ -10,6 +13,24 @@
 namespace aao {
 
 struct Handle;
+
+// A named NVTX range over a host scope (the solve, an outer iteration, the P_tilde phases, the
+// matvec): profilers that record NVTX can select kernels by phase (ncu --nvtx --nvtx-include).
+// Without such a profiler attached the calls do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Debug switch: with AAO_POISON_WORKSPACE set (and not "0") every device allocation of a handle
+// starts filled with 0xFF bytes (NaN in every floating-point type), so that a read of workspace
+// before its first write shows up as NaN in the results.
+inline bool poison_workspace() {
+    const char* v = std::getenv("AAO_POISON_WORKSPACE");
+    return v && v[0] && !(v[0] == '0' && v[1] == 0);
+}
 
 // Device memory owned by a handle; freed in reverse order at destroy.
 struct Arena {
@@ -25,6 +46,16 @@ struct Arena {
             set_error(std::string("cudaMalloc of ") + std::to_string(n * sizeof(T)) + " bytes failed: " +
                       cudaGetErrorString(e));
             return AAO_ERR_OOM;
+        }
+        if (poison_workspace()) {
+            // the fill runs on the legacy stream: wait for it before any stream of the handle runs
+            e = cudaMemset(q, 0xFF, n * sizeof(T));
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) {
+                cudaFree(q);
+                set_error(std::string("workspace poisoning failed: ") + cudaGetErrorString(e));
+                return AAO_ERR_CUDA;
+            }
         }
         ptrs.push_back(q);
         bytes += n * sizeof(T);

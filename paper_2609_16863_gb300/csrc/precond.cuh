@@ -891,7 +891,10 @@ class Precond : public PrecondBase {
         const long long nx = g.nx, nv = h->nv, item = (long long)s * nx;
         cudaEventRecord(e0, st());
         if (!transpose) {
-            AAO_TRY(inner<double>(nt, r + nv, item, z + nv, item, 0));
+            {
+                NvtxRange range_("aao.precond.theta_phase");
+                AAO_TRY(inner<double>(nt, r + nv, item, z + nv, item, 0));
+            }
             cudaEventRecord(e1, st());
             long long tot = (nt + 1) * nx;
             if (h->q1) {
@@ -907,7 +910,10 @@ class Precond : public PrecondBase {
             }
             launch(k_step_set, 1, 1, 0, st(), stepp, z, r, 0);
             AAO_LAUNCH_CHECK();
-            AAO_TRY(schur_sweep(0));
+            {
+                NvtxRange range_("aao.precond.schur_sweep");
+                AAO_TRY(schur_sweep(0));
+            }
             cudaEventRecord(e2, st());
         } else {
             // S_tilde^T: backward substitution, u stored in z's v-part (M = I: z_v = u)
@@ -915,7 +921,10 @@ class Precond : public PrecondBase {
                                          st()));
             launch(k_step_set, 1, 1, 0, st(), stepp, z, r, nt - 1);
             AAO_LAUNCH_CHECK();
-            AAO_TRY(schur_sweep(1));
+            {
+                NvtxRange range_("aao.precond.schur_sweep_transposed");
+                AAO_TRY(schur_sweep(1));
+            }
             cudaEventRecord(e1, st());
             long long tot = (long long)nt * item;
             if (h->q1) {
@@ -932,7 +941,10 @@ class Precond : public PrecondBase {
                        (const double*)z, (const double*)h->d_b, h->tau, tV);
             }
             AAO_LAUNCH_CHECK();
-            AAO_TRY(inner<A>(nt, tV, item, z + nv, item, 1));
+            {
+                NvtxRange range_("aao.precond.theta_phase_transposed");
+                AAO_TRY(inner<A>(nt, tV, item, z + nv, item, 1));
+            }
             cudaEventRecord(e2, st());
         }
         return AAO_OK;

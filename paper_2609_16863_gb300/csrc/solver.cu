@@ -395,6 +395,7 @@ static aao_status setup_handle(Handle* h, const aao_grid* grid, double tau, int 
 
 // ---------------------------------------------------------------------------
 static aao_status matvec_dev(Handle* h, const double* x, double* y, const double* rhs, int transpose) {
+    NvtxRange range_("aao.matvec");
     const Geo& g = h->g;
     if (h->q1) {
         bytes_hint(8.0 * h->nst * (rhs ? 3 : 2));
@@ -442,6 +443,7 @@ static aao_status read_small(Handle* h, SmallDev* sd) {
 // Restarted FGMRES (Algorithm 1, P_L = I, P_R = P_tilde or P_tilde^T), FP64.
 static aao_status fgmres(Handle* h, const double* b, double* x, int x0_given, int transpose, aao_info* info,
                          SmallDev* sd) {
+    NvtxRange range_(transpose ? "aao.fgmres_adjoint" : "aao.fgmres");
     auto t0 = std::chrono::steady_clock::now();
     const long long nst = h->nst;
     const int n0 = h->g.n0, m = h->m;
@@ -498,21 +500,24 @@ static aao_status fgmres(Handle* h, const double* b, double* x, int x0_given, in
             AAO_LAUNCH_CHECK();
             bool stop = false;
             for (int k = 0; k < m; ++k) {
+                NvtxRange iter_("aao.outer_iteration");
                 ++total;
                 double* Vk = h->V + (long long)k * nst;
                 double* Zk = h->Z + (long long)k * nst;
                 AAO_TRY(h->P->apply(Vk, Zk, transpose));
                 AAO_TRY(matvec_dev(h, Zk, h->w, nullptr, transpose));
-                Vec<double> none{};
-                Vec<double> Vfirst{h->V, nullptr, nst};
-                launch(k_mgs<double, double>, rgrid, kBlock, 0, st, n0, rows, 1, nullptr, h->w, nst, none, nullptr,
-                                                                Vfirst, 0, red, h->H + k);
-                for (int i = 1; i <= k + 1; ++i) {
-                    Vec<double> Vp{h->V + (long long)(i - 1) * nst, nullptr, nst};
-                    Vec<double> Vn = i <= k ? Vec<double>{h->V + (long long)i * nst, nullptr, nst} : none;
-                    launch(k_mgs<double, double>, rgrid, kBlock, 0, st, n0, rows, 1, nullptr, h->w, nst, Vp,
-                                                                    h->H + (i - 1) * m + k, Vn, 0, red,
-                                                                    h->H + i * m + k);
+                {
+                    NvtxRange ortho_("aao.orthogonalize");
+                    Vec<double> none{};
+                    Vec<double> Vfirst{h->V, nullptr, nst};
+                    launch(k_mgs<double, double>, rgrid, kBlock, 0, st, n0, rows, 1, nullptr, h->w, nst, none,
+                           nullptr, Vfirst, 0, red, h->H + k);
+                    for (int i = 1; i <= k + 1; ++i) {
+                        Vec<double> Vp{h->V + (long long)(i - 1) * nst, nullptr, nst};
+                        Vec<double> Vn = i <= k ? Vec<double>{h->V + (long long)i * nst, nullptr, nst} : none;
+                        launch(k_mgs<double, double>, rgrid, kBlock, 0, st, n0, rows, 1, nullptr, h->w, nst, Vp,
+                               h->H + (i - 1) * m + k, Vn, 0, red, h->H + i * m + k);
+                    }
                 }
                 launch(k_givens, 1, 32, 0, st, 1, k, m, h->H, 0, h->cs, h->sn, h->gv, h->beta + 1, tol, h->flags,
                                            h->flags + 1, h->flags + 2, h->resid);
