@@ -1,4 +1,4 @@
-"""Oracle solve driver: problem set-up + FGMRES with P_tilde (Sec. 3, Sec. 5).
+"""Oracle solve entry point: problem set-up + FGMRES with P_tilde (Sec. 3, Sec. 5).
 
 Test infrastructure only (see the package header).
 """
