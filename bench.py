@@ -200,7 +200,8 @@ def cpu_baseline(w, outer_its: int, budget_s: float = 20.0):
     est = outer_its * (2 * w.nt * t_inner + 2 * t_mv) + t_dot * outer_its * (outer_its + 1) / 2
     return {"value": est, "unit": "s", "cores": round(cores, 2), "kind": "oracle",
             "sample": (f"FP64 oracle (NumPy/SciPy) on the host: 1 full matvec ({t_mv:.2f} s) and {n_inner} inner "
-                       f"Theta_tilde solves ({t_inner:.3f} s each) at 256x256 s=3; time to solution estimated for "
+                       f"Theta_tilde solves ({t_inner:.3f} s each) at {'x'.join(map(str, w.n))} s={w.s}; time to "
+                       f"solution estimated for "
                        f"{outer_its} outer iterations as its*(2*nt*t_inner+2*t_matvec)+orthogonalisation")}
 
 
