@@ -25,7 +25,9 @@ def _window_solver(cache, cfg, kappa, nt_w):
         c = dict(cfg)
         c["nt"] = nt_w
         c["T"] = cfg["T"] * nt_w / cfg["nt"]          # same step tau
-        c["maxit"] = max(cfg.get("maxit", 100), 200)   # same tolerance as the forward solve
+        # the recomputed window must reach the forward solve's tolerance (a window that stops short
+        # raises), so it may take more outer iterations than the forward solve's cap
+        c["maxit"] = max(cfg.get("maxit", 100), 200)
         cache[nt_w] = Solver(kappa=kappa, **c)
     return cache[nt_w]
 
