@@ -17,20 +17,26 @@ from . import _lib
 from .tableau import make as make_tableau
 
 
-def _ptr(a):
-    """Address of a contiguous float64 torch tensor or numpy array (None -> NULL)."""
+def _ptr(a, n=None, what="vector"):
+    """Address of a contiguous float64 torch tensor or numpy array (None -> NULL).  With n given
+    the vector must hold at least n values: the library reads or writes exactly n values through
+    the address and cannot check the length itself."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
         if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
             raise TypeError("numpy vectors must be contiguous float64")
-        return a.ctypes.data
-    import torch
-    if isinstance(a, torch.Tensor):
+        size, addr = a.size, a.ctypes.data
+    else:
+        import torch
+        if not isinstance(a, torch.Tensor):
+            raise TypeError(f"unsupported vector type {type(a)}")
         if a.dtype != torch.float64 or not a.is_contiguous():
             raise TypeError("torch vectors must be contiguous float64")
-        return a.data_ptr()
-    raise TypeError(f"unsupported vector type {type(a)}")
+        size, addr = a.numel(), a.data_ptr()
+    if n is not None and size < n:
+        raise ValueError(f"{what} holds {size} values, {n} are needed")
+    return addr
 
 
 @dataclass
@@ -62,6 +68,7 @@ class Solver:
         self._lib = _lib.lib()
         self.n = tuple(int(v) for v in n)
         self.dim = len(self.n)
+        self.n_nodes = int(np.prod([v + 2 for v in self.n]))    # nodal kappa, boundary included
         A, b, c = tableau if tableau is not None else make_tableau(method, s)
         A, b, c = np.asarray(A, float), np.asarray(b, float), np.asarray(c, float)
         self.s = len(b)
@@ -74,7 +81,7 @@ class Solver:
             g.len[a] = (lens[a] if lens is not None else 1.0) if a < self.dim else 1.0
         g.disc = _lib.DISC[disc]
         self._kappa = kappa     # keep alive until set-up copied it
-        g.kappa = _ptr(kappa)
+        g.kappa = _ptr(kappa, self.n_nodes, "kappa")
         t = _lib.aao_tableau()
         t.s = self.s
         for i in range(self.s):
@@ -99,6 +106,10 @@ class Solver:
         _lib.check(self._lib.aao_rk_sizes(h, C.byref(nx), C.byref(nst)))
         self.nx, self.n_st = nx.value, nst.value
         self.n_v = (self.nt + 1) * self.nx
+
+    def _n_f(self, f_time_dep):
+        """Length of a source: one spatial field, or one per stage and time step."""
+        return self.nt * self.s * self.nx if f_time_dep else self.nx
 
     def close(self):
         if getattr(self, "h", None):
@@ -125,56 +136,64 @@ class Solver:
         _lib.check(self._lib.aao_rk_set_options(self.h, C.byref(o)))
 
     def rhs(self, f, u0, out, f_time_dep=False):
-        _lib.check(self._lib.aao_rk_rhs(self.h, _ptr(f), int(f_time_dep), _ptr(u0), _ptr(out)))
+        _lib.check(self._lib.aao_rk_rhs(self.h, _ptr(f, self._n_f(f_time_dep), "f"), int(f_time_dep),
+                                        _ptr(u0, self.nx, "u0"), _ptr(out, self.n_st, "out")))
         return out
 
     def matvec(self, x, y, transpose=False):
         fn = self._lib.aao_rk_matvec_transpose if transpose else self._lib.aao_rk_matvec
-        _lib.check(fn(self.h, _ptr(x), _ptr(y)))
+        _lib.check(fn(self.h, _ptr(x, self.n_st, "x"), _ptr(y, self.n_st, "y")))
         return y
 
     def precond_apply(self, r, z, transpose=False):
         fn = self._lib.aao_rk_precond_apply_transpose if transpose else self._lib.aao_rk_precond_apply
-        _lib.check(fn(self.h, _ptr(r), _ptr(z)))
+        _lib.check(fn(self.h, _ptr(r, self.n_st, "r"), _ptr(z, self.n_st, "z")))
         return z
 
     def shifted_solve(self, stage, b, x):
-        _lib.check(self._lib.aao_rk_shifted_solve(self.h, int(stage), _ptr(b), _ptr(x)))
+        _lib.check(self._lib.aao_rk_shifted_solve(self.h, int(stage), _ptr(b, self.nx, "b"),
+                                                  _ptr(x, self.nx, "x")))
         return x
 
     def pint_apply(self, r, y, transpose=False):
-        _lib.check(self._lib.aao_rk_pint_apply(self.h, _ptr(r), _ptr(y), int(transpose)))
+        n = self.s * self.nx
+        _lib.check(self._lib.aao_rk_pint_apply(self.h, _ptr(r, n, "r"), _ptr(y, n, "y"), int(transpose)))
         return y
 
     def inner_solve(self, nblocks, r, z):
         its = (C.c_int * nblocks)()
-        _lib.check(self._lib.aao_rk_inner_solve(self.h, int(nblocks), _ptr(r), _ptr(z), its))
+        n = int(nblocks) * self.s * self.nx
+        _lib.check(self._lib.aao_rk_inner_solve(self.h, int(nblocks), _ptr(r, n, "r"), _ptr(z, n, "z"), its))
         return z, list(its)
 
     # -- solves ---------------------------------------------------------------------
     def solve(self, f, u0, x, x0_given=False, f_time_dep=False, allow_not_converged=False):
         info = _lib.aao_info()
-        _lib.check(self._lib.aao_rk_solve(self.h, _ptr(f), int(f_time_dep), _ptr(u0), _ptr(x), int(x0_given),
+        _lib.check(self._lib.aao_rk_solve(self.h, _ptr(f, self._n_f(f_time_dep), "f"), int(f_time_dep),
+                                          _ptr(u0, self.nx, "u0"), _ptr(x, self.n_st, "x"), int(x0_given),
                                           C.byref(info)),
                    allow=(-4,) if allow_not_converged else ())
         return x, Info.from_c(info)
 
     def solve_rhs(self, rhs, x, x0_given=False, allow_not_converged=False):
         info = _lib.aao_info()
-        _lib.check(self._lib.aao_rk_solve_rhs(self.h, _ptr(rhs), _ptr(x), int(x0_given), C.byref(info)),
+        _lib.check(self._lib.aao_rk_solve_rhs(self.h, _ptr(rhs, self.n_st, "rhs"), _ptr(x, self.n_st, "x"),
+                                              int(x0_given), C.byref(info)),
                    allow=(-4,) if allow_not_converged else ())
         return x, Info.from_c(info)
 
     def adjoint_solve(self, dJdx, lam, x_fwd=None, grad_f=None, grad_kappa=None, allow_not_converged=False):
         info = _lib.aao_info()
-        _lib.check(self._lib.aao_rk_adjoint_solve(self.h, _ptr(dJdx), _ptr(lam), _ptr(x_fwd), _ptr(grad_f),
-                                                  _ptr(grad_kappa), C.byref(info)),
+        _lib.check(self._lib.aao_rk_adjoint_solve(self.h, _ptr(dJdx, self.n_st, "dJdx"), _ptr(lam, self.n_st, "lam"),
+                                                  _ptr(x_fwd, self.n_st, "x_fwd"), _ptr(grad_f, self.nx, "grad_f"),
+                                                  _ptr(grad_kappa, self.n_nodes, "grad_kappa"), C.byref(info)),
                    allow=(-4,) if allow_not_converged else ())
         return lam, Info.from_c(info)
 
 
     def grad_kappa(self, lam, x_fwd, out, accumulate=False):
-        _lib.check(self._lib.aao_rk_grad_kappa(self.h, _ptr(lam), _ptr(x_fwd), _ptr(out), int(accumulate)))
+        _lib.check(self._lib.aao_rk_grad_kappa(self.h, _ptr(lam, self.n_st, "lam"), _ptr(x_fwd, self.n_st, "x_fwd"),
+                                               _ptr(out, self.n_nodes, "out"), int(accumulate)))
         return out
 
 
@@ -183,9 +202,11 @@ def solve_batched(solvers, fs, u0s, xs):
     lib = _lib.lib()
     n = len(solvers)
     hs = (C.c_void_p * n)(*[s.h for s in solvers])
-    F = (C.c_void_p * n)(*[_ptr(f) for f in fs])
-    U = (C.c_void_p * n)(*[_ptr(u) for u in u0s])
-    X = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    if not (len(fs) == len(u0s) == len(xs) == n):
+        raise ValueError("one f, u0 and x per solver")
+    F = (C.c_void_p * n)(*[_ptr(f, s.nx, "f") for f, s in zip(fs, solvers)])
+    U = (C.c_void_p * n)(*[_ptr(u, s.nx, "u0") for u, s in zip(u0s, solvers)])
+    X = (C.c_void_p * n)(*[_ptr(x, s.n_st, "x") for x, s in zip(xs, solvers)])
     infos = (_lib.aao_info * n)()
     _lib.check(lib.aao_rk_solve_batched(n, hs, F, U, X, infos))
     return [Info.from_c(i) for i in infos]
