@@ -94,7 +94,9 @@ typedef struct {
     int cheb_steps;      /* Chebyshev steps for M^{-1} (Q1) */
     int prec_P;          /* aao_prec of Theta_tilde's GMRES and the S_tilde recurrence */
     int prec_Pint;       /* aao_prec of Rana's sweep, the V-cycles and coarse stencils */
-    int ckpt_every;      /* adjoint: keep every k-th forward state (0 = keep all) */
+    int ckpt_every;      /* must be 0 (else AAO_ERR_UNSUPPORTED): a checkpointed kappa gradient is
+                          * summed by the caller over windows of steps recomputed from kept
+                          * states, one aao_rk_grad_kappa(accumulate = 1) call per window */
     void* stream;        /* cudaStream_t for every call on the handle; NULL = default stream */
 } aao_options;
 

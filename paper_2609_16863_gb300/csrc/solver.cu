@@ -251,6 +251,11 @@ static aao_status validate(const aao_grid* grid, double tau, int nt, const aao_t
         set_error("a 16-bit P_tilde needs the same 16-bit P_int");
         return AAO_ERR_ARG;
     }
+    if (o->ckpt_every != 0) {
+        set_error("ckpt_every must be 0: checkpointed gradients are summed by the caller over windows "
+                  "(aao_rk_grad_kappa with accumulate)");
+        return AAO_ERR_UNSUPPORTED;
+    }
     return AAO_OK;
 }
 

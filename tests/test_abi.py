@@ -202,3 +202,12 @@ def test_batched_rejects_a_repeated_handle(lib):
     vec = (ctypes.c_void_p * 3)(0x3000, 0x3000, 0x3000)
     assert L.aao_rk_solve_batched(3, hs, vec, vec, vec, None) == -1
     assert b"more than once" in L.aao_rk_last_error()
+
+
+def test_setup_rejects_library_side_checkpointing(lib):
+    L, g, t, o = _valid_setup_args()
+    o.ckpt_every = 4
+    h = ctypes.c_void_p()
+    st = L.aao_rk_setup(ctypes.byref(g), 0.1, 4, ctypes.byref(t), ctypes.byref(o), ctypes.byref(h))
+    assert st == -8 and not h.value
+    assert b"aao_rk_grad_kappa" in L.aao_rk_last_error()
