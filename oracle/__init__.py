@@ -22,7 +22,8 @@ It is a plain, slow, obviously-correct restatement of the method:
 * ``mgrit``      -- two-level multigrid reduction in time for S_tilde's time
                     recurrence (the parallel implementation of Sec. 5).
 * ``fgmres``     -- restarted right-preconditioned flexible GMRES (Algorithm 1
-                    with P_L = I, P_R = P_tilde).
+                    with P_L = I, P_R = P_tilde), and Algorithm 1 with a left
+                    (or split) preconditioner.
 * ``sequential`` -- sequential RK time stepping with direct stage solves.
 * ``adjoint``    -- the adjoint solve and gradients of the tracking functional.
 
