@@ -24,7 +24,10 @@ It is a plain, slow, obviously-correct restatement of the method:
 * ``fgmres``     -- restarted right-preconditioned flexible GMRES (Algorithm 1
                     with P_L = I, P_R = P_tilde), and Algorithm 1 with a left
                     (or split) preconditioner.
-* ``sequential`` -- sequential RK time stepping with direct stage solves.
+* ``sequential`` -- sequential RK time stepping with direct stage solves, its
+                    adjoint, and forward substitution for any right-hand side.
+* ``problems``   -- the paper's exact-solution test problem of Sec. 5.1 with Q1 or
+                    Q2 elements (Table 2's DoF, time grids and errors).
 * ``adjoint``    -- the adjoint solve and gradients of the tracking functional.
 
 Parity status per function is stated in each module header.  There is no

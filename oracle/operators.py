@@ -13,6 +13,8 @@ mass matrix (Eq. discretized_system_stages).  Two discretisations:
 * Q1 finite elements on a tensor mesh: the 1D linear-element matrices
   M1 = h/6 tridiag(1, 4, 1), K1 = 1/h tridiag(-1, 2, -1) restricted to the
   interior nodes, and M = (x)_a M1_a, K = sum_a (x)_{b != a} M1_b (x) K1_a.
+* Q2 finite elements (Sec. 5: the paper's second element family) on the same
+  tensor construction with 1D quadratic elements (vertex and midpoint nodes).
 
 Layout: lexicographic with x fastest; Kronecker products therefore list the
 slowest axis first (kron(Ay, Ax) in 2D).
@@ -112,6 +114,43 @@ def q1_matrices(ns, lens=None):
     return M.tocsr(), K.tocsr()
 
 
+def _q2_1d(n: int, h: float):
+    """1D quadratic Lagrange elements on n interior nodes of spacing h (n odd): (n + 1) / 2 elements
+    of size H = 2h, nodes (left, midpoint, right).  Element matrices (exact integrals):
+    mass H/30 [[4, 2, -1], [2, 16, 2], [-1, 2, 4]], stiffness 1/(3H) [[7, -8, 1], [-8, 16, -8],
+    [1, -8, 7]]; assembled on all 2E + 1 nodes, then restricted to the interior ones."""
+    if n % 2 != 1:
+        raise ValueError("Q2 elements need an odd number of interior nodes per axis")
+    E = (n + 1) // 2
+    H = 2.0 * h
+    Me = H / 30.0 * np.array([[4.0, 2.0, -1.0], [2.0, 16.0, 2.0], [-1.0, 2.0, 4.0]])
+    Ke = 1.0 / (3.0 * H) * np.array([[7.0, -8.0, 1.0], [-8.0, 16.0, -8.0], [1.0, -8.0, 7.0]])
+    N = 2 * E + 1
+    M = np.zeros((N, N))
+    K = np.zeros((N, N))
+    for e in range(E):
+        idx = [2 * e, 2 * e + 1, 2 * e + 2]
+        M[np.ix_(idx, idx)] += Me
+        K[np.ix_(idx, idx)] += Ke
+    return sp.csr_matrix(M[1:-1, 1:-1]), sp.csr_matrix(K[1:-1, 1:-1])
+
+
+def q2_matrices(ns, lens=None):
+    """(M, K) for biquadratic/triquadratic elements on the tensor mesh whose interior nodes (element
+    vertices and midpoints) are the vertex grid of `ns` (every n odd)."""
+    ns = tuple(int(n) for n in ns)
+    hs = spacing(ns, lens)
+    ones = [_q2_1d(n, h) for n, h in zip(ns, hs)]
+    d = len(ns)
+    M = reduce(lambda X, Y: sp.kron(X, Y, format="csr"), [ones[a][0] for a in reversed(range(d))])
+    K = None
+    for a in range(d):
+        facs = [ones[b][1] if b == a else ones[b][0] for b in reversed(range(d))]
+        term = reduce(lambda X, Y: sp.kron(X, Y, format="csr"), facs)
+        K = term if K is None else K + term
+    return M.tocsr(), K.tocsr()
+
+
 def q1_jacobi_interval(d: int):
     """Spectrum bounds of D^{-1} M for the Q1 mass matrix: [2^-d, (3/2)^d]."""
     return 0.5 ** d, 1.5 ** d
@@ -121,8 +160,8 @@ def operators(ns, lens=None, disc: str = "fd", kappa=None):
     """Return (M, K) as CSR; M is None to mean the identity (FD)."""
     if disc == "fd":
         return None, stiffness_fd(ns, lens, kappa)
-    if disc == "q1":
+    if disc in ("q1", "q2"):
         if kappa is not None:
             raise ValueError("variable kappa is only defined for the FD discretisation")
-        return q1_matrices(ns, lens)
+        return q1_matrices(ns, lens) if disc == "q1" else q2_matrices(ns, lens)
     raise ValueError(disc)

@@ -58,3 +58,25 @@ def sequential_adjoint_rk(op, g):
         KL = sum(op.K.T @ Lam[n, i] for i in range(s))
         mu[n] = solveMT(gv[n] + Mmu - KL)
     return op.join(mu, Lam)
+
+
+def sequential_solve(op, rhs):
+    """x = A^{-1} rhs for any right-hand side by forward substitution in time with direct solves.
+
+    The rows of the all-at-once operator (Sec. 2) give, for rhs = [r_v ; r_V]:
+      M v_0 = r_{v,0};
+      Theta_hat V_n = r_{V,n} - (e (x) K) v_n;
+      M v_{n+1} = M v_n + tau sum_i b_i M V_{n,i} + r_{v,n+1}."""
+    nt, s, nx, tau, b = op.nt, op.s, op.nx, op.tau, op.b
+    rv, rV = op.split(np.asarray(rhs, dtype=np.float64))
+    lu = spla.splu(op.theta_hat().tocsc())
+    luM = None if op.M is None else spla.splu(op.M.tocsc())
+    solveM = (lambda r: r.copy()) if luM is None else luM.solve
+    v = np.zeros((nt + 1, nx))
+    V = np.zeros((nt, s, nx))
+    v[0] = solveM(rv[0])
+    for n in range(nt):
+        Kv = op.K @ v[n]
+        V[n] = lu.solve(np.concatenate([rV[n, i] - Kv for i in range(s)])).reshape(s, nx)
+        v[n + 1] = v[n] + tau * sum(b[i] * V[n, i] for i in range(s)) + solveM(rv[n + 1])
+    return op.join(v, V)
