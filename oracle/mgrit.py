@@ -24,11 +24,15 @@ Reading (the paper is silent):
 * Phi_c, the coarse propagator, is supplied by the caller (for S_tilde: the same step with step
   size m tau, i.e. Theta_tilde and its multigrid rebuilt for the shifts m tau d_i).
 
+`vcycle` / `multilevel` are the multilevel form (XBraid's default): the coarse error equation is
+itself solved by one V-cycle, down to a level solved by substitution.
+
 Parity: pinned (tests) by the exactness property of MGRIT -- after k iterations the first
 (2k+1)m points (FCF) or (k+1)m points (F) equal sequential substitution, for any Phi_c with
 Phi_c(0) = 0 -- by one-iteration convergence with the ideal coarse propagator Phi_c = Phi^m for a
-linear Phi, and by the coarse S_tilde step on sine eigenmodes against the RK stability function
-R(-m tau lambda).
+linear Phi (two levels) and Phi^m, Phi^(m^2) (three levels), by the coarse S_tilde step on sine
+eigenmodes against the RK stability function R(-m tau lambda), and by the multilevel cycle with
+two levels being the two-level method bit for bit.
 """
 from __future__ import annotations
 
@@ -86,4 +90,48 @@ def sequential(phi, w):
     u[0] = w[0]
     for n in range(w.shape[0] - 1):
         u[n + 1] = phi(u[n]) + w[n + 1]
+    return u
+
+
+def vcycle(phis, w, m: int, relax: str = "FCF", u=None):
+    """One multilevel MGRIT V-cycle (Falgout et al. 2014) for u_0 = w_0, u_{n+1} = phis[0](u_n) +
+    w_{n+1}.  phis[k] is the propagator of level k (step size m^k tau); level k has nt / m^k steps
+    and the last level is solved by substitution.  On every other level: relaxation, the C-point
+    residuals, one V-cycle for the coarse error equation e_0 = 0, e_j = phis[k+1](e_{j-1}) + r_j from
+    a zero guess, the C-point correction u_{jm} += e_j and an F-relaxation (ideal interpolation).
+    With two levels this is one iteration of `two_level` followed by its final F-relaxation."""
+    w = np.asarray(w, dtype=np.float64)
+    nt = w.shape[0] - 1
+    if u is None:
+        u = np.zeros_like(w)
+        u[0] = w[0]
+    else:
+        u = np.array(u, dtype=np.float64)
+    if len(phis) == 1:
+        return sequential(phis[0], w)
+    if m < 1 or nt % m != 0:
+        raise ValueError("the coarsening factor must divide the number of time steps on every level")
+    if relax not in ("F", "FCF"):
+        raise ValueError("relaxation is 'F' or 'FCF'")
+    phi = phis[0]
+    nc = nt // m
+    f_relax(phi, u, w, m)
+    if relax == "FCF":
+        c_relax(phi, u, w, m)
+        f_relax(phi, u, w, m)
+    r = np.zeros((nc + 1,) + w.shape[1:])
+    for j in range(1, nc + 1):
+        r[j] = w[j * m] + phi(u[j * m - 1]) - u[j * m]
+    e = vcycle(phis[1:], r, m, relax)
+    for j in range(1, nc + 1):
+        u[j * m] = u[j * m] + e[j]
+    f_relax(phi, u, w, m)
+    return u
+
+
+def multilevel(phis, w, m: int, iters: int = 1, relax: str = "FCF"):
+    """`iters` multilevel V-cycles from the zero guess (u_0 = w_0)."""
+    u = None
+    for _ in range(iters):
+        u = vcycle(phis, w, m, relax, u)
     return u

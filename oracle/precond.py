@@ -115,7 +115,7 @@ class Preconditioner:
 
     def __init__(self, op, ns, inner_maxit=3, inner_tol=1e-3, mg_cycles=3, nu1=2, nu2=2,
                  omega=2.0 / 3.0, cheb_steps=20, exact=False, schur="sequential", mgrit_m=8,
-                 mgrit_iters=1, mgrit_relax="FCF"):
+                 mgrit_iters=1, mgrit_relax="FCF", mgrit_levels=2):
         self.op = op
         self.ns = tuple(ns)
         self.s, self.nt, self.nx = op.s, op.nt, op.nx
@@ -144,13 +144,18 @@ class Preconditioner:
             raise ValueError("schur is 'sequential' or 'mgrit'")
         self.schur = schur
         self.mgrit_m, self.mgrit_iters, self.mgrit_relax = int(mgrit_m), int(mgrit_iters), mgrit_relax
+        self.mgrit_levels = int(mgrit_levels)
         self.coarse = None
+        self.coarser = []          # levels 1 .. mgrit_levels-1: steps of size m^k tau
         if schur == "mgrit":
-            if self.mgrit_m < 1 or self.nt % self.mgrit_m != 0:
-                raise ValueError("the MGRIT coarsening factor must divide nt")
-            op_c = AllAtOnce(op.K, op.M, self.mgrit_m * op.tau, self.nt // self.mgrit_m, op.A, op.b, op.c)
-            self.coarse = Preconditioner(op_c, ns, inner_maxit, inner_tol, mg_cycles, nu1, nu2, omega,
-                                         cheb_steps, exact)
+            if self.mgrit_levels < 2 or self.mgrit_m < 1 or self.nt % self.mgrit_m ** (self.mgrit_levels - 1) != 0:
+                raise ValueError("the MGRIT coarsening factor m (to the power levels-1) must divide nt")
+            for k in range(1, self.mgrit_levels):
+                mk = self.mgrit_m ** k
+                op_k = AllAtOnce(op.K, op.M, mk * op.tau, self.nt // mk, op.A, op.b, op.c)
+                self.coarser.append(Preconditioner(op_k, ns, inner_maxit, inner_tol, mg_cycles, nu1, nu2, omega,
+                                                   cheb_steps, exact))
+            self.coarse = self.coarser[0]
 
     # -- spatial pieces -------------------------------------------------------
     def shifted_solve(self, i, r):
@@ -245,8 +250,12 @@ class Preconditioner:
             g[n + 1] = rv[n + 1] + tau * op.Mmul(acc)
         w = np.stack([self.mass_inverse(g[n]) for n in range(nt + 1)])
         if self.schur == "mgrit":
-            zv = mgrit.two_level(self.schur_step, self.coarse.schur_step, w, self.mgrit_m,
-                                 self.mgrit_iters, self.mgrit_relax)
+            if self.mgrit_levels == 2:
+                zv = mgrit.two_level(self.schur_step, self.coarse.schur_step, w, self.mgrit_m,
+                                     self.mgrit_iters, self.mgrit_relax)
+            else:
+                zv = mgrit.multilevel([self.schur_step] + [c.schur_step for c in self.coarser], w,
+                                      self.mgrit_m, self.mgrit_iters, self.mgrit_relax)
             return op.join(zv, zV)
         zv = np.empty_like(rv)
         zv[0] = w[0]
@@ -285,8 +294,12 @@ class Preconditioner:
         nt, s, nx, tau, b = self.nt, self.s, self.nx, op.tau, op.b
         if self.schur == "mgrit":
             # the backward recurrence is a forward one in reversed time
-            u = mgrit.two_level(self.schur_step_T, self.coarse.schur_step_T, rv[::-1], self.mgrit_m,
-                                self.mgrit_iters, self.mgrit_relax)[::-1]
+            if self.mgrit_levels == 2:
+                u = mgrit.two_level(self.schur_step_T, self.coarse.schur_step_T, rv[::-1], self.mgrit_m,
+                                    self.mgrit_iters, self.mgrit_relax)[::-1]
+            else:
+                u = mgrit.multilevel([self.schur_step_T] + [c.schur_step_T for c in self.coarser], rv[::-1],
+                                     self.mgrit_m, self.mgrit_iters, self.mgrit_relax)[::-1]
         else:
             u = np.empty_like(rv)
             u[nt] = rv[nt]

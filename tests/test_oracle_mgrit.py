@@ -116,3 +116,48 @@ def test_mgrit_rejects_bad_parameters():
     op = build(NS, 1.0, 6, "radau", 2)
     with pytest.raises(ValueError):
         Preconditioner(op, NS, schur="mgrit", mgrit_m=4)
+
+
+@pytest.mark.parametrize("relax,iters", [("FCF", 1), ("F", 2)])
+def test_multilevel_with_two_levels_is_two_level(relax, iters):
+    nt, m = 24, 4
+    op, P = _precond(nt, m)
+    w = np.stack([synth.random_vector(op.nx, 300 + n) for n in range(nt + 1)])
+    a = mgrit.two_level(P.schur_step, P.coarse.schur_step, w, m, iters, relax)
+    b = mgrit.multilevel([P.schur_step, P.coarse.schur_step], w, m, iters, relax)
+    assert np.array_equal(a, b)
+
+
+def test_three_levels_with_ideal_propagators_converge_in_one_cycle():
+    """Linear Phi (exact stage solves), level propagators Phi^m and Phi^(m^2): one V-cycle is exact."""
+    nt, m = 18, 3
+    op, P = _precond(nt, m, exact=True)
+
+    def power(k):
+        def f(e):
+            for _ in range(k):
+                e = P.schur_step(e)
+            return e
+        return f
+
+    w = np.stack([synth.random_vector(op.nx, 400 + n) for n in range(nt + 1)])
+    u = mgrit.multilevel([P.schur_step, power(m), power(m * m)], w, m, 1, "F")
+    assert _rel(u, mgrit.sequential(P.schur_step, w)) <= 1e-12
+
+
+def test_three_level_preconditioner_converges_to_substitution():
+    """Three levels with steps tau, 3 tau, 9 tau (re-discretised): V-cycles contract towards the
+    substitution, and P_tilde / P_tilde^T with enough cycles equal the sequential ones."""
+    nt, m = 18, 3
+    op, P = _precond(nt, m, s=2, mgrit_levels=3)
+    w = np.stack([synth.random_vector(op.nx, 500 + n) for n in range(nt + 1)])
+    phis = [P.schur_step] + [c.schur_step for c in P.coarser]
+    ref = mgrit.sequential(P.schur_step, w)
+    errs = [_rel(mgrit.multilevel(phis, w, m, k, "FCF"), ref) for k in (1, 2, 3)]
+    assert errs[0] < 1e-2 and errs[1] < 0.1 * errs[0] and errs[2] < 0.1 * errs[1]
+    P9 = Preconditioner(op, NS, inner_maxit=3, inner_tol=0.0, mg_cycles=3, nu1=2, nu2=2, omega=0.8,
+                        schur="mgrit", mgrit_m=m, mgrit_levels=3, mgrit_iters=4)
+    Pseq = Preconditioner(op, NS, inner_maxit=3, inner_tol=0.0, mg_cycles=3, nu1=2, nu2=2, omega=0.8)
+    r = synth.random_vector(op.n_st, 8)
+    assert _rel(P9.apply(r), Pseq.apply(r)) <= 1e-9
+    assert _rel(P9.apply_T(r), Pseq.apply_T(r)) <= 1e-9
