@@ -30,6 +30,14 @@
  *
  * Errors: every call returns an aao_status; the text of the last error of the
  * calling thread is returned by aao_rk_last_error().  No call aborts or traps.
+ *
+ * Profiling and debugging: host NVTX ranges name the phases (aao.fgmres,
+ * aao.outer_iteration, aao.orthogonalize, aao.matvec, aao.precond.theta_phase,
+ * aao.precond.schur_sweep and the transposed pair) for profilers that record
+ * NVTX; aao_rk_profile_begin/end time the launches of chosen kernels.  With
+ * the environment variable AAO_POISON_WORKSPACE set (not "0") every device
+ * allocation of a handle starts filled with 0xFF bytes (NaN), so a read of
+ * workspace before its first write shows in the results.
  */
 #ifndef AAO_RK_H
 #define AAO_RK_H
