@@ -156,6 +156,13 @@ def q1_jacobi_interval(d: int):
     return 0.5 ** d, 1.5 ** d
 
 
+def q2_jacobi_interval(d: int):
+    """Spectrum bounds of D^{-1} M for the Q2 mass matrix: [2^-d, (5/4)^d].  Element by element
+    (D = sum of the element diagonals), the 1D element pencil diag(M_e)^{-1} M_e has eigenvalues
+    1/2, 5/4, 5/4; the tensor product multiplies the 1D bounds."""
+    return 0.5 ** d, 1.25 ** d
+
+
 def operators(ns, lens=None, disc: str = "fd", kappa=None):
     """Return (M, K) as CSR; M is None to mean the identity (FD)."""
     if disc == "fd":

@@ -169,7 +169,8 @@ class Preconditioner:
             return g.copy()
         if self.exact:
             return self.lu_M.solve(g)
-        return chebyshev_jacobi(self.op.M, g, self.cheb_steps, *q1_jacobi_interval(len(self.ns)))
+        interval = getattr(self.op, "mass_interval", None) or q1_jacobi_interval(len(self.ns))
+        return chebyshev_jacobi(self.op.M, g, self.cheb_steps, *interval)
 
     # -- stage pieces ---------------------------------------------------------
     def theta_apply(self, z):

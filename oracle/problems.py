@@ -32,7 +32,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from .aao import AllAtOnce
-from .operators import operators
+from .operators import operators, q1_jacobi_interval, q2_jacobi_interval
 from .tableau import tableau
 
 T_FINAL = 2.0
@@ -121,6 +121,7 @@ def exact_solution_problem(disc: str, l: int, s: int, tf: float = T_FINAL, quad:
     nt = time_steps(disc, l, s, tf)
     A, b, c = tableau("radau", s)
     op = AllAtOnce(K, M, tf / nt, nt, A, b, c)
+    op.mass_interval = (q1_jacobi_interval if disc == "q1" else q2_jacobi_interval)(2)
     X = np.arange(1, n + 1) * (LENGTH / (n + 1))
     prof1 = np.sin(math.pi * X / 2.0)
     g1 = load_1d(disc, n, lambda Z: np.sin(math.pi * Z / 2.0), LENGTH, quad)

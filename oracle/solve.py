@@ -10,7 +10,7 @@ import numpy as np
 
 from .aao import AllAtOnce
 from .fgmres import fgmres
-from .operators import operators
+from .operators import operators, q2_jacobi_interval
 from .precond import Preconditioner
 from .tableau import tableau
 
@@ -44,7 +44,10 @@ def build(ns, T, nt, method, s, disc="fd", kappa=None, lens=None, tab=None):
     """AllAtOnce operator for the heat problem; tab = (A, b, c) overrides the tableau."""
     M, K = operators(ns, lens, disc, kappa)
     A, b, c = tab if tab is not None else tableau(method, s)
-    return AllAtOnce(K, M, T / nt, nt, A, b, c)
+    op = AllAtOnce(K, M, T / nt, nt, A, b, c)
+    if disc == "q2":
+        op.mass_interval = q2_jacobi_interval(len(ns))
+    return op
 
 
 def solve(op, ns, rhs, opts: OracleOptions, x0=None, transpose=False):

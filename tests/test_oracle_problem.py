@@ -84,3 +84,37 @@ def test_convergence_order_in_h(disc, s, order):
         errs.append(P.v_error(sequential_solve(P.op, P.rhs())))
     for a, b in zip(errs, errs[1:]):
         assert a / b >= 0.85 * 2 ** order, (errs, order)
+
+
+def test_chebyshev_mass_inverse_bound_q2():
+    """||e_k||_M <= ||e_0||_M / T_k(sigma) with the Q2 interval [1/4, 25/16] (element-by-element
+    bound of D^{-1} M), on the assembled 2D Q2 mass matrix."""
+    import scipy.sparse.linalg as spla
+    from oracle.operators import q2_jacobi_interval
+    from oracle.precond import chebyshev_jacobi
+    M, _ = q2_matrices((15, 13), (1.0, 2.0))
+    A = M.toarray()
+    ev = np.linalg.eigvals(np.linalg.solve(np.diag(np.diag(A)), A)).real
+    lo, hi = q2_jacobi_interval(2)
+    assert lo <= ev.min() and ev.max() <= hi * (1 + 1e-12)
+    g = np.random.default_rng(2).standard_normal(M.shape[0])
+    x = spla.spsolve(M.tocsc(), g)
+    sig = (hi + lo) / (hi - lo)
+    for k in (5, 10, 20):
+        e = x - chebyshev_jacobi(M, g, k, lo, hi)
+        ratio = np.sqrt(e @ (M @ e) / (x @ (M @ x)))
+        assert ratio <= 1.0 / np.cosh(k * np.arccosh(sig)) * 1.01
+
+
+@pytest.mark.parametrize("disc,s,l", [("q2", 2, 3), ("q1", 3, 4)])
+def test_preconditioned_solve_of_the_exact_solution_problem(disc, s, l):
+    """FGMRES with P_tilde (multigrid, Chebyshev M^{-1} with the element's interval) on the paper's
+    problem reaches the direct solution."""
+    from oracle.fgmres import fgmres
+    from oracle.precond import Preconditioner
+    P = exact_solution_problem(disc, l, s)
+    pre = Preconditioner(P.op, (P.n, P.n), inner_maxit=5, inner_tol=1e-6, omega=0.8)
+    x, its, rr, ok = fgmres(P.op.matvec, pre.apply, P.rhs(), 1e-12, 20, 100)
+    ref = sequential_solve(P.op, P.rhs())
+    assert ok and np.abs(x - ref).max() <= 1e-9 * np.abs(ref).max()
+    assert abs(P.v_error(x) - P.v_error(ref)) <= 1e-6 * P.v_error(ref)
