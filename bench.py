@@ -111,6 +111,17 @@ def batched_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest of every rank's value (each rank times its own replica); world == 1: itself."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -307,11 +318,7 @@ def main():
     barrier()
     ck = clocks.stop()
     launches = lib.aao_rk_launch_count() - n0
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     x_mixed = x.clone()
 
     # FP64 preconditioner on the same problem (mixed vs FP64 comparison)
@@ -419,7 +426,7 @@ def main():
                 "outer_its": info.outer_its, "inner_its": info.inner_its_total, "rel_res": info.rel_res,
                 "t_theta_ms": info.t_theta_ms, "t_schur_ms": info.t_schur_ms,
                 "fp64_precond": fp64,
-                "dofs_its_per_s": S.n_st * info.outer_its / (ms / 1e3),
+                "dofs_its_per_s": world * S.n_st * info.outer_its / (ms / 1e3),   # all replicas
                 "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * (2 * S.nx),
                         "d2h_bytes_per_step": 8 * S.n_st},
                 "gpu_launches": launches // max(1, args.steps) * args.steps,
