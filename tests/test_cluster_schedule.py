@@ -25,7 +25,7 @@ import pytest
 
 import synth
 from oracle.multigrid import Hierarchy, level_sizes
-from oracle.operators import mass_fd, stiffness_fd
+from oracle.operators import mass_fd, q1_matrices, stiffness_fd
 
 
 def plan(ns, C):
@@ -316,7 +316,10 @@ def cluster_vcycles(H, b, cycles, C, rlo):
     return x.ravel(), mem.races
 
 
-def _hierarchy(ns, nu1, nu2, kappa=False, shift=0.05 / 128):
+def _hierarchy(ns, nu1, nu2, kappa=False, shift=0.05 / 128, q1=False):
+    if q1:                                  # 9-point fine level (the kernel's stored fine stencil)
+        M, K = q1_matrices(ns)
+        return Hierarchy((M + shift * K).tocsr(), ns, 0.8, nu1, nu2)
     kap = None
     if kappa:
         kap = np.exp(synth.gaussian_random_field(ns, 0.15, 0.5, synth.rng_for(3, "kappa"), with_boundary=True))
@@ -324,14 +327,15 @@ def _hierarchy(ns, nu1, nu2, kappa=False, shift=0.05 / 128):
     return Hierarchy(A, ns, 0.8, nu1, nu2)
 
 
-@pytest.mark.parametrize("ns,C,nu1,nu2,kappa", [
-    ((40, 36), 16, 2, 2, False), ((40, 36), 16, 0, 1, False), ((40, 36), 16, 1, 0, False),
-    ((40, 36), 16, 0, 0, False), ((34, 37), 16, 2, 2, True), ((120, 17), 8, 2, 2, False),
-    ((36, 70), 16, 1, 3, False)])
-def test_cluster_schedule_matches_oracle(ns, C, nu1, nu2, kappa):
+@pytest.mark.parametrize("ns,C,nu1,nu2,kind", [
+    ((40, 36), 16, 2, 2, "fd"), ((40, 36), 16, 0, 1, "fd"), ((40, 36), 16, 1, 0, "fd"),
+    ((40, 36), 16, 0, 0, "fd"), ((34, 37), 16, 2, 2, "kappa"), ((120, 17), 8, 2, 2, "fd"),
+    ((36, 70), 16, 1, 3, "fd"), ((40, 36), 16, 2, 2, "q1"), ((120, 17), 8, 0, 1, "q1")])
+def test_cluster_schedule_matches_oracle(ns, C, nu1, nu2, kind):
+    """FD (5-point fine level, constant or kappa field) and Q1 (9-point fine level, stored)."""
     sizes, rlo = plan(ns, C)
     assert rlo is not None
-    H = _hierarchy(ns, nu1, nu2, kappa)
+    H = _hierarchy(ns, nu1, nu2, kappa=kind == "kappa", q1=kind == "q1")
     b = synth.random_vector(int(np.prod(ns)), 70)
     x, races = cluster_vcycles(H, b, 2, C, rlo)
     assert not races, races[:3]
