@@ -205,7 +205,8 @@ aao_status aao_rk_grad_kappa(aao_rk_handle h, const double* lambda, const double
  * non-OK status, after every problem has been attempted.  Problems run on up
  * to 64 host threads, largest (space-time unknowns) first; each handle may
  * appear once.  nprob == 0 is a no-op returning AAO_OK; nprob < 0, NULL
- * arrays, a NULL or repeated handle give AAO_ERR_ARG before any device work. */
+ * arrays, a NULL or repeated handle, or an open launch profile
+ * (aao_rk_profile_begin) give AAO_ERR_ARG before any device work. */
 aao_status aao_rk_solve_batched(int nprob, const aao_rk_handle* hs, const double* const* f,
                                 const double* const* u0, double* const* x, aao_info* infos);
 

@@ -978,6 +978,11 @@ aao_status aao_rk_solve_batched(int nprob, const aao_rk_handle* hs, const double
         }
     }
     if (nprob == 0) return AAO_OK;
+    if (g_prof_on) {
+        // the launch profile's bookkeeping is not shared between threads
+        set_error("batched solves run on several threads: close the launch profile first");
+        return AAO_ERR_ARG;
+    }
     int dev = 0;
     AAO_CUDA_TRY(cudaGetDevice(&dev));
     // Host worker threads, one per problem up to kMaxBatchThreads: every

@@ -211,3 +211,16 @@ def test_setup_rejects_library_side_checkpointing(lib):
     st = L.aao_rk_setup(ctypes.byref(g), 0.1, 4, ctypes.byref(t), ctypes.byref(o), ctypes.byref(h))
     assert st == -8 and not h.value
     assert b"aao_rk_grad_kappa" in L.aao_rk_last_error()
+
+
+def test_batched_refuses_while_a_launch_profile_is_open(lib):
+    from paper_2609_16863_gb300 import _lib
+    L = _lib.load()
+    assert L.aao_rk_profile_begin(b"k_cluster_mg") == 0
+    try:
+        hs = (ctypes.c_void_p * 2)(0x1000, 0x2000)          # never dereferenced: rejected first
+        vec = (ctypes.c_void_p * 2)(0x3000, 0x3000)
+        assert L.aao_rk_solve_batched(2, hs, vec, vec, vec, None) == -1
+        assert b"launch profile" in L.aao_rk_last_error()
+    finally:
+        L.aao_rk_profile_end(None, None, None)              # closes the profile (no device here)
