@@ -161,3 +161,16 @@ def test_three_level_preconditioner_converges_to_substitution():
     r = synth.random_vector(op.n_st, 8)
     assert _rel(P9.apply(r), Pseq.apply(r)) <= 1e-9
     assert _rel(P9.apply_T(r), Pseq.apply_T(r)) <= 1e-9
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_mgrit_transposed_preconditioner_in_an_adjoint_solve(levels):
+    """FGMRES on A^T with P_tilde^T using MGRIT (two or three levels) reaches the dense transposed
+    solution: MGRIT changes only the path."""
+    from oracle.fgmres import fgmres
+    nt, m = 9, 3
+    op, P = _precond(nt, m, s=2, mgrit_levels=levels)
+    g = synth.random_vector(op.n_st, 12)
+    lam, its, rr, ok = fgmres(op.rmatvec, P.apply_T, g, 1e-11, 20, 100)
+    ref = np.linalg.solve(op.dense().T, g)
+    assert ok and np.linalg.norm(lam - ref) <= 1e-8 * np.linalg.norm(ref)
