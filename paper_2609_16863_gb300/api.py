@@ -136,31 +136,38 @@ class Solver:
         _lib.check(self._lib.aao_rk_set_options(self.h, C.byref(o)))
 
     def rhs(self, f, u0, out, f_time_dep=False):
+        """out (n_st) = the all-at-once right-hand side [M u0 ; 0 ; M f at every stage] for the source f
+        (n_x values, or nt*s*n_x at the stage times with f_time_dep) and initial data u0 (n_x)."""
         _lib.check(self._lib.aao_rk_rhs(self.h, _ptr(f, self._n_f(f_time_dep), "f"), int(f_time_dep),
                                         _ptr(u0, self.nx, "u0"), _ptr(out, self.n_st, "out")))
         return out
 
     def matvec(self, x, y, transpose=False):
+        """y = A x (or A^T x), FP64, n_st values each."""
         fn = self._lib.aao_rk_matvec_transpose if transpose else self._lib.aao_rk_matvec
         _lib.check(fn(self.h, _ptr(x, self.n_st, "x"), _ptr(y, self.n_st, "y")))
         return y
 
     def precond_apply(self, r, z, transpose=False):
+        """z = P_tilde^{-1} r (or P_tilde^{-T} r), n_st values each."""
         fn = self._lib.aao_rk_precond_apply_transpose if transpose else self._lib.aao_rk_precond_apply
         _lib.check(fn(self.h, _ptr(r, self.n_st, "r"), _ptr(z, self.n_st, "z")))
         return z
 
     def shifted_solve(self, stage, b, x):
+        """x ~= (M + tau d_stage K)^{-1} b by the multigrid V-cycles (n_x values each)."""
         _lib.check(self._lib.aao_rk_shifted_solve(self.h, int(stage), _ptr(b, self.nx, "b"),
                                                   _ptr(x, self.nx, "x")))
         return x
 
     def pint_apply(self, r, y, transpose=False):
+        """y = P_int^{-1} r (or P_int^{-T} r) for one time step, s*n_x values each."""
         n = self.s * self.nx
         _lib.check(self._lib.aao_rk_pint_apply(self.h, _ptr(r, n, "r"), _ptr(y, n, "y"), int(transpose)))
         return y
 
     def inner_solve(self, nblocks, r, z):
+        """z_n = Theta_tilde^{-1} r_n for nblocks time blocks of s*n_x values; returns (z, iterations)."""
         its = (C.c_int * nblocks)()
         n = int(nblocks) * self.s * self.nx
         _lib.check(self._lib.aao_rk_inner_solve(self.h, int(nblocks), _ptr(r, n, "r"), _ptr(z, n, "z"), its))
@@ -168,6 +175,8 @@ class Solver:
 
     # -- solves ---------------------------------------------------------------------
     def solve(self, f, u0, x, x0_given=False, f_time_dep=False, allow_not_converged=False):
+        """Solve A x = rhs(f, u0) by FGMRES with P_tilde; x (n_st) is the initial guess with x0_given.
+        Returns (x, Info); raises AaoError on failure (not on non-convergence with allow_not_converged)."""
         info = _lib.aao_info()
         _lib.check(self._lib.aao_rk_solve(self.h, _ptr(f, self._n_f(f_time_dep), "f"), int(f_time_dep),
                                           _ptr(u0, self.nx, "u0"), _ptr(x, self.n_st, "x"), int(x0_given),
@@ -176,6 +185,7 @@ class Solver:
         return x, Info.from_c(info)
 
     def solve_rhs(self, rhs, x, x0_given=False, allow_not_converged=False):
+        """Solve A x = rhs for a given all-at-once right-hand side (n_st values)."""
         info = _lib.aao_info()
         _lib.check(self._lib.aao_rk_solve_rhs(self.h, _ptr(rhs, self.n_st, "rhs"), _ptr(x, self.n_st, "x"),
                                               int(x0_given), C.byref(info)),
@@ -183,6 +193,8 @@ class Solver:
         return x, Info.from_c(info)
 
     def adjoint_solve(self, dJdx, lam, x_fwd=None, grad_f=None, grad_kappa=None, allow_not_converged=False):
+        """Solve A^T lam = dJdx (n_st) with P_tilde^T; optionally the gradients with respect to f (n_x) and,
+        given the forward solution x_fwd, to the nodal kappa (prod(n + 2) values)."""
         info = _lib.aao_info()
         _lib.check(self._lib.aao_rk_adjoint_solve(self.h, _ptr(dJdx, self.n_st, "dJdx"), _ptr(lam, self.n_st, "lam"),
                                                   _ptr(x_fwd, self.n_st, "x_fwd"), _ptr(grad_f, self.nx, "grad_f"),
@@ -190,8 +202,8 @@ class Solver:
                    allow=(-4,) if allow_not_converged else ())
         return lam, Info.from_c(info)
 
-
     def grad_kappa(self, lam, x_fwd, out, accumulate=False):
+        """out (+)= dJ/dkappa at the nodes from the adjoint lam and the forward solution x_fwd (n_st each)."""
         _lib.check(self._lib.aao_rk_grad_kappa(self.h, _ptr(lam, self.n_st, "lam"), _ptr(x_fwd, self.n_st, "x_fwd"),
                                                _ptr(out, self.n_nodes, "out"), int(accumulate)))
         return out
