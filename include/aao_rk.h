@@ -230,13 +230,19 @@ aao_status aao_rk_inner_solve(aao_rk_handle h, int nblocks, const double* r, dou
  * needs no handle and calls no allocating routine.  All scratch lives in one
  * fixed 5 MiB device array inside the library, which every GPU that loads the
  * library keeps until the process exits; grids above 65536 points (or whose
- * coarsest level exceeds 256 points) are rejected with AAO_ERR_ARG.  b and x
- * are device memory (n_x values, host pointers are rejected), the work is
- * queued on `stream` (NULL = default stream).  The first call on a device looks
- * up the array's device address, so make it before any stream capture.  Every
- * call reuses the same array: calls that overlap on the GPU (other streams,
- * other threads) race and must be serialised by the caller.  The scratch keeps
- * the last call's contents; each call rebuilds what it reads. */
+ * coarsest level exceeds 256 points) are rejected with AAO_ERR_ARG, as are
+ * lengths that are not finite and positive, and a c or omega that is not
+ * finite.  b and x are device memory of the current device (n_x values; host
+ * pointers and other GPUs' memory are rejected), the work is queued on
+ * `stream` (NULL = default stream) and the call returns once it has finished:
+ * it reads back the coarsest level's inversion flag and returns
+ * AAO_ERR_BREAKDOWN if that operator is not positive definite.  The first call
+ * on a device looks up the array's device address, so make it before any
+ * stream capture; the address is kept for the process, so do not use this
+ * entry point across a cudaDeviceReset.  Every call reuses the same array:
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller.  The scratch keeps the last call's contents;
+ * each call rebuilds what it reads and clears the flag it reads back. */
 aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double c, int cycles, int pre, int post,
                                         double omega, const double* b, double* x, void* stream);
 

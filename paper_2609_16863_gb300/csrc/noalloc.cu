@@ -8,6 +8,7 @@
 // (level vectors, Galerkin stencils, the coarsest dense inverse) in one
 // file-scope __device__ array of fixed size, g_noalloc_scratch below.  Every
 // GPU that loads the library holds that array until the process exits.
+#include <cmath>
 #include <mutex>
 
 #include "handle.cuh"
@@ -22,7 +23,10 @@ constexpr long long kNoAllocMaxPoints = 65536;
 constexpr int kNoAllocMaxCoarsest = kCoarsestTarget;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
-// Device address of g_noalloc_scratch per device, looked up once per device.
+// Device address of g_noalloc_scratch per device, looked up once per device (the
+// first call on that device).  The address stays valid for the life of the
+// device's primary context: after cudaDeviceReset it may be stale, so the
+// allocation-free entry point must not be used across a device reset.
 static double* g_noalloc_ptr[64] = {};
 static std::mutex g_noalloc_mutex;
 
@@ -48,13 +52,22 @@ static aao_status noalloc_scratch(double** out) {
     return AAO_OK;
 }
 
+// Device (or managed) memory of the current device.  Memory of another GPU is
+// refused: without peer access the kernels could not read it.
 static bool device_pointer(const void* p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    if (at.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.device == dev;
 }
 
 }  // namespace aao
@@ -75,10 +88,16 @@ extern "C" aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double 
         set_error("the allocation-free solve supports the constant-coefficient FD grid only");
         return AAO_ERR_ARG;
     }
-    if (!(c >= 0.0) || cycles < 1 || pre < 0 || post < 0 || !(omega > 0.0)) {
-        set_error("need c >= 0, cycles >= 1, pre/post >= 0, omega > 0");
+    if (!(c >= 0.0) || !std::isfinite(c) || cycles < 1 || pre < 0 || post < 0 || !(omega > 0.0) ||
+        !std::isfinite(omega)) {
+        set_error("need a finite c >= 0, cycles >= 1, pre/post >= 0 and a finite omega > 0");
         return AAO_ERR_ARG;
     }
+    for (int a = 0; a < grid->dim; ++a)
+        if (!(grid->len[a] > 0.0) || !std::isfinite(grid->len[a])) {
+            set_error("grid lengths must be finite and positive");
+            return AAO_ERR_ARG;
+        }
     Geo g;
     g.d = grid->dim;
     g.n0 = grid->n[0];
@@ -173,6 +192,8 @@ extern "C" aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double 
         fd.sten = sten[l];
     }
     launch(k_dense_level, (unsigned)((nc + 127) / 128), 128, 0, st, fd, dense);
+    // the scratch keeps the previous call's contents: the breakdown flag must start at zero
+    AAO_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), st));
     launch(k_gauss_jordan, 1, 1024, 0, st, dense, dinv, nc, fail);
     AAO_LAUNCH_CHECK();
     LevelOp<double> ops[kMaxLevels];
@@ -253,6 +274,15 @@ extern "C" aao_status aao_rk_shifted_solve_noalloc(const aao_grid* grid, double 
     for (int cyc = 0; cyc < cycles; ++cyc) {
         AAO_TRY(Rec::run(0, L, lev, cyc == 0 ? Vec<double>{} : xv, bv, xv, T0, T1, Rr, Bb, X, dinv, pre, post,
                          omega, st, ops));
+    }
+    // the coarsest operator's inversion reports a zero or negative pivot in the flag: read it
+    // back (the call therefore returns after its work on `stream` has finished)
+    int hfail = 0;
+    AAO_CUDA_TRY(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AAO_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hfail) {
+        set_error("coarsest multigrid operator is not positive definite");
+        return AAO_ERR_BREAKDOWN;
     }
     return AAO_OK;
 }

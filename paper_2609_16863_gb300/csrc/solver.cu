@@ -181,6 +181,9 @@ __global__ void k_pack_small(const double* resid, const int* flags, const double
     out->beta = beta[0];
 }
 
+// Device memory of the current device (or managed memory).  Device memory of
+// another GPU is not taken as device memory: without peer access the kernels
+// could not read it.
 static bool is_device_ptr(const void* p) {
     if (p == nullptr) return false;
     cudaPointerAttributes at;
@@ -189,7 +192,14 @@ static bool is_device_ptr(const void* p) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    if (at.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.device == dev;
 }
 
 // ---------------------------------------------------------------------------
@@ -204,8 +214,8 @@ static aao_status validate(const aao_grid* grid, double tau, int nt, const aao_t
         return AAO_ERR_ARG;
     }
     for (int a = 0; a < grid->dim; ++a)
-        if (grid->n[a] < 1 || !(grid->len[a] > 0.0)) {
-            set_error("grid sizes and lengths must be positive");
+        if (grid->n[a] < 1 || !(grid->len[a] > 0.0) || !std::isfinite(grid->len[a])) {
+            set_error("grid sizes and lengths must be positive (lengths finite)");
             return AAO_ERR_ARG;
         }
     if (grid->disc != AAO_DISC_FD && grid->disc != AAO_DISC_Q1) {

@@ -99,6 +99,7 @@ def _set(obj, field, value):
 SETUP_BAD = [
     ("grid.dim", 1, b"dim"), ("grid.dim", 4, b"dim"), ("grid.n[1]", 0, b"grid sizes"),
     ("grid.len[0]", -1.0, b"grid sizes"), ("grid.len[1]", float("nan"), b"grid sizes"),
+    ("grid.len[0]", float("inf"), b"grid sizes"),
     ("grid.disc", 7, b"discretisation"), ("q1_kappa", None, b"kappa"),
     ("tau", 0.0, b"tau"), ("tau", float("nan"), b"tau"), ("nt", 0, b"tau"), ("nt", 65535, b"65534"),
     ("tab.s", 0, b"stages"), ("tab.s", 9, b"stages"),
@@ -146,7 +147,8 @@ def test_setup_validation_table(lib, what, value, words):
 NOALLOC_BAD = [
     ("null_grid", b"null"), ("dim", b"dim"), ("kappa", b"constant-coefficient"), ("q1", b"constant-coefficient"),
     ("c", b"c >= 0"), ("cycles", b"cycles"), ("pre", b"pre/post"), ("omega", b"omega"),
-    ("size0", b"positive"), ("too_large", b"65536"),
+    ("size0", b"positive"), ("too_large", b"65536"), ("len0", b"lengths"), ("len_inf", b"lengths"),
+    ("len_nan", b"lengths"), ("c_inf", b"finite c"),
 ]
 
 
@@ -175,6 +177,14 @@ def test_noalloc_validation_table(lib, what, words):
         g.n[0] = 0
     elif what == "too_large":
         g.n[0], g.n[1] = 300, 300
+    elif what == "len0":
+        g.len[0] = 0.0
+    elif what == "len_inf":
+        g.len[1] = float("inf")
+    elif what == "len_nan":
+        g.len[0] = float("nan")
+    elif what == "c_inf":
+        args["c"] = float("inf")
     dummy = ctypes.c_void_p(0x1000)       # never dereferenced: rejected first
     st = L.aao_rk_shifted_solve_noalloc(gp, ctypes.c_double(args["c"]), args["cycles"], args["pre"], args["post"],
                                         ctypes.c_double(args["omega"]), dummy, dummy, None)

@@ -1,5 +1,5 @@
 """The allocation-free shifted solve (aao_rk_shifted_solve_noalloc) against the
-handle-based aao_rk_shifted_solve.
+handle-based aao_rk_shifted_solve and against the oracle's V-cycles.
 
 The allocation-free entry point is for callers that cannot call cudaMalloc
 (pools that forbid it, hosts that only hand out pre-registered buffers,
@@ -34,6 +34,9 @@ def _grid(ns):
 
 @pytest.mark.parametrize("ns", [(48, 40), (256, 256), (12, 10, 14)])
 def test_noalloc_matches_handle_shifted_solve_twice(ns):
+    import scipy.sparse as sp
+    from oracle.multigrid import Hierarchy
+    from oracle.operators import operators
     from paper_2609_16863_gb300 import Solver, _lib, radau_iia
     dev()
     lib = _lib.lib()
@@ -42,15 +45,20 @@ def test_noalloc_matches_handle_shifted_solve_twice(ns):
     A, _, _ = radau_iia(s)
     c = (T / nt) * A[0, 0]           # shift of stage 1: tau * d_1, d_1 = a_11 (first LDU pivot)
     g = _grid(ns)
+    _, K = operators(ns)
+    mg = Hierarchy(sp.identity(S.nx, format="csr") + c * K, ns, omega=0.8, nu1=2, nu2=2)
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):            # two calls in a row share (and must reset) the scratch
-        b = to_dev(synth.random_vector(S.nx, 90 + call))
+        bh = synth.random_vector(S.nx, 90 + call)
+        b = to_dev(bh)
         ref = host(S.shifted_solve(0, b, zeros(S.nx)))
         x = zeros(S.nx)
         st = lib.aao_rk_shifted_solve_noalloc(C.byref(g), c, 3, 2, 2, 0.8, C.c_void_p(b.data_ptr()),
                                              C.c_void_p(x.data_ptr()), C.c_void_p(stream))
         _lib.check(st)
-        assert rel_max(host(x), ref) <= 1e-12
+        xh = host(x)
+        assert rel_max(xh, ref) <= 1e-12
+        assert rel_max(xh, mg.solve(bh, 3)) <= 1e-12
 
 
 def test_noalloc_rejects_oversize_and_host_buffers():
