@@ -29,9 +29,11 @@ It is a plain, slow, obviously-correct restatement of the method:
 * ``problems``   -- the paper's exact-solution test problem of Sec. 5.1 with Q1 or
                     Q2 elements (Table 2's DoF, time grids and errors).
 * ``adjoint``    -- the adjoint solve and gradients of the tracking functional.
+* ``spectral``   -- the exact all-at-once solution for constant-coefficient finite
+                    differences, mode by mode in the sine basis (any size).
+* ``lowprec``    -- P_tilde with its stored vectors rounded to FP32, BF16 or FP16
+                    (per-row power-of-two scales) and FP32 arithmetic, the storage
+                    emulation of Sec. 4--5 (the paper simulates it with chop).
 
-Parity status per function is stated in each module header.  There is no
-low-precision emulation here: the GPU path's FP32/BF16/FP16 storage is
-compared with these FP64 results at tolerances set by the storage precision's
-unit roundoff.
+Parity status per function is stated in each module header.
 """
