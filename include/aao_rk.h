@@ -106,6 +106,11 @@ typedef struct {
                           * summed by the caller over windows of steps recomputed from kept
                           * states, one aao_rk_grad_kappa(accumulate = 1) call per window */
     void* stream;        /* cudaStream_t for every call on the handle; NULL = default stream */
+    int mgrit_m;         /* S_tilde's time recurrence: 0 = forward substitution (Eq. AppSchur);
+                          * m >= 2 (m divides nt) = one two-level MGRIT iteration with coarsening
+                          * factor m and F-relaxation, the coarse step being the same substitution
+                          * step with step size m tau (the parallel implementation of Sec. 5);
+                          * P_tilde^T runs it on the backward recurrence in reversed time */
 } aao_options;
 
 typedef struct {
@@ -150,8 +155,9 @@ const char* aao_rk_profile_report(void);
 
 /* n_x = prod(n), n_st = n_x (nt + 1 + s nt). */
 aao_status aao_rk_sizes(aao_rk_handle h, long long* n_x, long long* n_st);
-/* Replace tol / restart / maxit / inner_* / stream (precisions and multigrid
- * shape are fixed at set-up; changing them returns AAO_ERR_ARG). */
+/* Replace tol / restart / maxit / inner_tol (precisions, multigrid shape,
+ * inner_maxit, mgrit_m and the stream are fixed at set-up; changing them
+ * returns AAO_ERR_ARG). */
 aao_status aao_rk_set_options(aao_rk_handle h, const aao_options* opts);
 
 /* rhs = [M u0 ; 0 .. 0 ; M f_{n,i}] (Sec. 2 with zero Dirichlet data).  f has

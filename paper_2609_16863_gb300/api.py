@@ -58,13 +58,15 @@ class Info:
 
 class Solver:
     """Handle for one problem: grid n (interior points per axis), final time T,
-    nt steps, an RK tableau (A, b, c), optional nodal diffusivity kappa."""
+    nt steps, an RK tableau (A, b, c), optional nodal diffusivity kappa.  mgrit_m > 0
+    (a divisor of nt) replaces S_tilde's forward substitution by one two-level MGRIT
+    iteration with coarsening factor mgrit_m."""
 
     def __init__(self, n: Sequence[int], T: float, nt: int, tableau=None, method: str = "radau", s: int = 2,
                  lens=None, kappa=None, prec_P: str = "fp64", prec_Pint: Optional[str] = None,
                  tol: float = 1e-8, restart: int = 20, maxit: int = 100, inner_maxit: int = 0,
                  inner_tol: float = -1.0, mg_cycles: int = 3, mg_pre: int = 2, mg_post: int = 2,
-                 mg_omega: float = 0.8, disc: str = "fd", cheb_steps: int = 20, stream=None):
+                 mg_omega: float = 0.8, disc: str = "fd", cheb_steps: int = 20, stream=None, mgrit_m: int = 0):
         self._lib = _lib.lib()
         self.n = tuple(int(v) for v in n)
         self.dim = len(self.n)
@@ -98,6 +100,7 @@ class Solver:
         o.prec_P = _lib.PREC[prec_P]
         o.prec_Pint = _lib.PREC[prec_Pint if prec_Pint is not None else prec_P]
         o.stream = stream
+        o.mgrit_m = mgrit_m
         self.options = o
         h = C.c_void_p()
         _lib.check(self._lib.aao_rk_setup(C.byref(g), self.tau, self.nt, C.byref(t), C.byref(o), C.byref(h)))

@@ -38,6 +38,7 @@ namespace aao {
 
 constexpr int kClMax = 16;            // CTAs per cluster (16 needs the non-portable size)
 constexpr int kClThreads = 512;
+constexpr int kClMaxBatch = 32;       // batches of at most this many items run one cluster per item
 
 template <class SI> struct ClCtx {
     using A = typename PT<SI>::A;
@@ -113,6 +114,13 @@ __device__ __forceinline__ unsigned cl_rank() {
     unsigned r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
     return r;
+}
+
+// Index of this CTA's cluster in the grid: the batch item the cluster solves.
+__device__ __forceinline__ int cl_item() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return (int)r;
 }
 
 __device__ __forceinline__ void cl_sync() {
@@ -355,12 +363,12 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) 
 // from the staged data.  Same values as the register path.
 template <class SI>
 __device__ __forceinline__ void cl_stage_async(const ClCtx<SI>& t, int rank, int L, int T, float* sm, const Vec<SI>& bv,
-                                               int tid, int nthr) {
+                                               int item, int tid, int nthr) {
     const Geo& g = t.g[0];
     const int a = t.rlo[0][rank], nr = t.rlo[0][rank + 1] - a;
     const int ld0 = g.n0 + 2, xs0 = (t.maxr[0] + 2) * ld0;
     float* B0 = sm + t.off[0] + 2 * xs0;
-    const float* bsrc = reinterpret_cast<const float*>(bv.d);
+    const float* bsrc = reinterpret_cast<const float*>(bv.d) + (long long)item * bv.bs;
     if (nr > 0) {
         const int nb0 = (nr + 2) * g.n0;
         for (int p = tid; p < nb0; p += nthr) {
@@ -423,7 +431,8 @@ __device__ __forceinline__ void cl_stage_async(const ClCtx<SI>& t, int rank, int
     }
 }
 
-// All mg_cycles V-cycles of (M + c K) x = b for one item, b and x in global memory.
+// All mg_cycles V-cycles of (M + c K) x = b, b and x in global memory: cluster k of the grid solves
+// batch item k (grid = C x items CTAs; clusters never wait on one another).
 template <class SI>
 __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* __restrict__ ctx, const int* active,
                                                               Vec<SI> bv, Vec<SI> xout) {
@@ -432,7 +441,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
     __shared__ ClShared<SI> S;
     extern __shared__ __align__(16) unsigned char cl_smem[];
     A* sm = reinterpret_cast<A*>(cl_smem);
-    if (active && !active[0]) return;         // the same decision in every CTA of the cluster
+    const int item = cl_item();               // one cluster per batch item
+    if (active && !active[item]) return;      // the same decision in every CTA of the cluster
     const int tid = threadIdx.x, nthr = blockDim.x;
     {
         const int* src = reinterpret_cast<const int*>(ctx);
@@ -497,7 +507,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
     __syncthreads();
     if (tid < L) S.lev[tid] = cl_level(S, sm, tid);
     if constexpr (std::is_same<SI, float>::value && std::is_same<typename PT<SI>::A, float>::value) {
-        cl_stage_async(t, rank, L, T, sm, bv, tid, nthr);
+        cl_stage_async(t, rank, L, T, sm, bv, item, tid, nthr);
     } else {
         // ---- stage b, faces, stencils, Jacobi weights and this CTA's rows of the coarsest inverse
         // (loads from global memory are issued in groups before the shared-memory stores)
@@ -506,7 +516,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
             const Geo& g = t.g[0];
             const int a = t.rlo[0][rank], nr = t.rlo[0][rank + 1] - a;
             const int np0 = nr * g.n0, ld0 = g.n0 + 2, xs0 = (t.maxr[0] + 2) * ld0;
-            View<SI> bs = view_of(bv, 0, 0, g.n0);
+            View<SI> bs = view_of(bv, item, 0, g.n0);
             A* B0 = sm + t.off[0] + 2 * xs0;
             // rows a-1 .. a+nr of b (the ghost rows too: the residual of a zero guess is b)
             const int nb0 = nr > 0 ? (nr + 2) * g.n0 : 0;
@@ -710,12 +720,12 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
             for (int lr = w; lr < v.nr; lr += nw) {
                 SI* o;
                 float* osc;
-                row_store_ptrs(xout, 0, 0, v.a + lr, v.n0, o, osc);
+                row_store_ptrs(xout, item, 0, v.a + lr, v.n0, o, osc);
                 const A* X = v.el(k, lr, 0);
                 row_store<SI>(o, osc, v.n0, lane, [&](int c) -> A { return X[c]; });
             }
         } else {
-            SI* o = xout.d + (long long)v.a * v.n0;
+            SI* o = xout.d + (long long)item * xout.bs + (long long)v.a * v.n0;
             for (int p = tid; p < v.nr * v.n0; p += nthr) {
                 const int lr = cl_div(p, v.magic);
                 o[p] = PT<SI>::st(*v.el(k, lr, p - lr * v.n0));

@@ -485,6 +485,117 @@ __global__ void __launch_bounds__(kBlock) k_schurT_update(Geo g, int s, const St
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched steps of the Schur recurrence (two-level MGRIT, the parallel form of
+// S_tilde in Sec. 5): B items of one step at once, item b at time index
+// n_b = sp->n + b * stride (forward; transposed: n_b = sp->n - b * stride), the
+// items' inner solves batched (blockIdx.y = item).  With `res` set, a step writes
+// the C-point residual w_{n+1} + Phi(z_n) - z_{n+1} of item b into block b + 1 of
+// res (transposed: block nres - 1 - b) instead of updating the recurrence.
+// ---------------------------------------------------------------------------
+template <class A>
+__global__ void __launch_bounds__(kBlock) k_schur_rhs_b(Geo g, int s, const StepPtrs* sp, int stride, A* t,
+                                                        SpaceOp<A> sop) {
+    pdl_prologue();
+    long long row = gwarp();
+    if (row >= g.R) return;
+    const int b = blockIdx.y;
+    int j, k;
+    row_jk(g, row, j, k);
+    View<double> z{sp->z + (long long)(sp->n + b * stride) * g.nx, nullptr, g.n0};
+    A* tb = t + (long long)b * s * g.nx;
+    for (int c = lane_id(); c < g.n0; c += kWarp) {
+        A v = (A)op_K(z, g, sop, row, j, k, c);
+        for (int i = 0; i < s; ++i) tb[(long long)i * g.nx + row * g.n0 + c] = v;
+    }
+}
+
+template <class SZ, class A>
+__global__ void __launch_bounds__(kBlock) k_schur_update_b(Geo g, int s, const A* wbuf, const StepPtrs* sp,
+                                                           int stride, Vec<SZ> Z0, long long zstride,
+                                                           const double* y, int kmax, const int* its,
+                                                           const double* bw, double tau, A* res) {
+    pdl_prologue();
+    long long row = gwarp();
+    if (row >= g.R) return;
+    const int b = blockIdx.y;
+    const int n = sp->n + b * stride;
+    const A* wn1 = wbuf + (long long)(n + 1) * g.nx;
+    const double* zvn = sp->z + (long long)n * g.nx;
+    double* zvn1 = sp->z + (long long)(n + 1) * g.nx;
+    const int m = its[b];
+    A coef[kMaxInner * kMaxS];
+    for (int k = 0; k < m; ++k)
+        for (int i = 0; i < s; ++i) coef[k * s + i] = (A)(tau * bw[i] * y[(long long)b * kmax + k]);
+    for (int c = lane_id(); c < g.n0; c += kWarp) {
+        long long p = row * g.n0 + c;
+        A acc = wn1[p] + (A)zvn[p];
+        for (int k = 0; k < m; ++k) {
+            Vec<SZ> Zk = Z0;
+            Zk.d += k * zstride;
+            if constexpr (PT<SZ>::scaled) Zk.sc += (k * zstride) / g.n0;
+            for (int i = 0; i < s; ++i) {
+                View<SZ> z = view_of(Zk, b, (long long)i * g.nx, g.n0);
+                acc -= coef[k * s + i] * z.at(row, c);
+            }
+        }
+        if (res) res[(long long)(b + 1) * g.nx + p] = acc - (A)zvn1[p];
+        else zvn1[p] = (double)acc;
+    }
+}
+
+// Transposed: t_{b,i} = b_i u_{n_b + 1}.
+template <class A>
+__global__ void k_schurT_rhs_b(long long nx, int s, const StepPtrs* sp, int stride, const double* bw, A* t) {
+    pdl_prologue();
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)s * nx) return;
+    const int b = blockIdx.y;
+    int q = (int)(i / nx);
+    t[(long long)b * s * nx + i] =
+        (A)bw[q] * (A)sp->z[(long long)(sp->n - b * stride + 1) * nx + i % nx];
+}
+
+// Transposed: u_{n_b} = r_{v,n_b} + u_{n_b+1} - tau sum_i K q_{b,i}  (or its C-point residual).
+template <class A>
+__global__ void __launch_bounds__(kBlock) k_schurT_update_b(Geo g, int s, const StepPtrs* sp, int stride,
+                                                            const A* q, double tau, SpaceOp<A> sop, double* res,
+                                                            int nres) {
+    pdl_prologue();
+    long long row = gwarp();
+    if (row >= g.R) return;
+    const int b = blockIdx.y;
+    int j, k;
+    row_jk(g, row, j, k);
+    const int n = sp->n - b * stride;
+    const double* rvn = sp->r + (long long)n * g.nx;
+    const double* un1 = sp->z + (long long)(n + 1) * g.nx;
+    double* un = sp->z + (long long)n * g.nx;
+    View<A> qs[kMaxS];
+    for (int i = 0; i < s; ++i) qs[i] = View<A>{q + ((long long)b * s + i) * g.nx, nullptr, g.n0};
+    for (int c = lane_id(); c < g.n0; c += kWarp) {
+        long long p = row * g.n0 + c;
+        A acc = A(0);
+        for (int i = 0; i < s; ++i) acc += (A)op_K(qs[i], g, sop, row, j, k, c);
+        const A v = (A)rvn[p] + (A)un1[p] - (A)tau * acc;
+        if (res) res[(long long)(nres - 1 - b) * g.nx + p] = (double)(v - (A)un[p]);
+        else un[p] = (double)v;
+    }
+}
+
+// MGRIT C-points: z_{z0 + zdir c m} (+)= e_{e0 + edir c} for c = 1..nc (e == nullptr: set to zero).
+static __global__ void k_mgrit_cpoints(double* z, const double* e, long long nx, int nc, int m, int z0, int zdir,
+                                       int e0, int edir) {
+    pdl_prologue();
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)nc * nx) return;
+    const int c = (int)(i / nx) + 1;
+    const long long p = i % nx;
+    double* zp = z + (long long)(z0 + zdir * c * m) * nx + p;
+    if (e) *zp += e[(long long)(e0 + edir * c) * nx + p];
+    else *zp = 0.0;
+}
+
 // t_{n,i} = r_{V,n,i} + tau b_i z_{v,n+1}  (all n at once, type A).
 template <class A>
 __global__ void k_schurT_vrhs(long long nx, int nt, int s, const double* rV, const double* zv, const double* bw,

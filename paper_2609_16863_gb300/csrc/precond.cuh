@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <type_traits>
 
 #include "cluster_mg.cuh"
@@ -84,9 +85,19 @@ class Precond : public PrecondBase {
 
     cudaStream_t cur_stream = nullptr;     // stream of the next launch (capture stream while capturing)
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    long long graph_nodes[2] = {0, 0};
+    // one captured graph per step kind [transpose][kind]: 0 one time step, 1 a batched MGRIT
+    // relaxation step, 2 the batched C-point residual step
+    cudaGraphExec_t gexec[2][3] = {};
+    long long graph_nodes[2][3] = {};
     StepPtrs* stepp = nullptr;
+    // two-level MGRIT for S_tilde's recurrence (mg_m = 0: forward substitution): the coarse
+    // propagator is the substitution step of a second preconditioner built for step size
+    // mg_m tau and mg_nc = nt / mg_m steps
+    int mg_m = 0, mg_nc = 0;
+    std::unique_ptr<Handle> hc;
+    Precond* coarse = nullptr;
+    double* ebuf = nullptr;        // (nc+1)*nx: coarse error recurrence
+    double* rbufT = nullptr;       // (nc+1)*nx: transposed C-point residuals (the coarse source)
 
     cudaStream_t st() const { return cur_stream; }
 
@@ -115,9 +126,14 @@ class Precond : public PrecondBase {
     ~Precond() override { release(); }
 
     void release() override {
+        if (coarse) delete coarse;
+        coarse = nullptr;
+        hc.reset();
         for (int i = 0; i < 2; ++i)
-            if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
-        gexec[0] = gexec[1] = nullptr;
+            for (int k = 0; k < 3; ++k) {
+                if (gexec[i][k]) cudaGraphExecDestroy(gexec[i][k]);
+                gexec[i][k] = nullptr;
+            }
         if (cap_stream) cudaStreamDestroy(cap_stream);
         cap_stream = nullptr;
         ar.release();
@@ -306,9 +322,14 @@ class Precond : public PrecondBase {
         AAO_CUDA_TRY(cudaMemsetAsync(nonfin, 0, 2 * sizeof(int), st()));
         AAO_CUDA_TRY(cudaMemsetAsync(itcount, 0, sizeof(long long), st()));
         // ---- Schur state
+        if (h->opt.mgrit_m > 0) {
+            mg_m = h->opt.mgrit_m;
+            mg_nc = h->nt / mg_m;
+        }
+        const long long steps_b = mg_nc > 1 ? mg_nc : 1;     // items of a batched step
         AAO_TRY(ar.alloc(&wbuf, (size_t)((h->nt + 1) * g0.nx)));
-        AAO_TRY(ar.alloc(&tbuf, (size_t)item));
-        AAO_TRY(ar.alloc(&qbuf, (size_t)item));
+        AAO_TRY(ar.alloc(&tbuf, (size_t)(steps_b * item)));
+        AAO_TRY(ar.alloc(&qbuf, (size_t)(steps_b * item)));
         AAO_TRY(ar.alloc(&tV, (size_t)(h->nt * item)));
         AAO_TRY(ar.alloc(&tmp64, (size_t)(Bmax * item)));
         AAO_TRY(ar.alloc(&stepp, 1));
@@ -318,6 +339,21 @@ class Precond : public PrecondBase {
         AAO_CUDA_TRY(cudaEventCreate(&e1));
         AAO_CUDA_TRY(cudaEventCreate(&e2));
         AAO_CUDA_TRY(cudaMallocHost((void**)&hact, sizeof(int) * Bmax));
+        if (mg_m > 0) {
+            // the coarse level of MGRIT: the same operators with step mg_m tau over mg_nc steps
+            hc.reset(new Handle(*h));
+            hc->arena = Arena();
+            hc->P = nullptr;
+            hc->nt = mg_nc;
+            hc->tau = mg_m * h->tau;
+            hc->nv = (long long)(mg_nc + 1) * g0.nx;
+            hc->nst = hc->nv + (long long)mg_nc * s * g0.nx;
+            hc->opt.mgrit_m = 0;
+            coarse = new Precond(hc.get());
+            AAO_TRY(coarse->setup());
+            AAO_TRY(ar.alloc(&ebuf, (size_t)((mg_nc + 1) * g0.nx)));
+            AAO_TRY(ar.alloc(&rbufT, (size_t)((mg_nc + 1) * g0.nx)));
+        }
         AAO_CUDA_TRY(cudaStreamSynchronize(st()));
         return AAO_OK;
     }
@@ -711,9 +747,10 @@ class Precond : public PrecondBase {
     }
 
     aao_status mg_solve(int stage, int B, const int* act, Vec<SI> b, Vec<SI> out) {
-        if (B == 1 && cl_C > 0) {
+        if (B <= kClMaxBatch && cl_C > 0) {
+            // one cluster per item: small batches (single time steps, MGRIT's batched steps)
             bytes_hint(2.0 * nact * h->g.nx * sizeof(SI));
-            launch_cluster(k_cluster_mg<SI>, dim3((unsigned)cl_C), dim3(kClThreads), cl_smem, st(), cl_C,
+            launch_cluster(k_cluster_mg<SI>, dim3((unsigned)(cl_C * B)), dim3(kClThreads), cl_smem, st(), cl_C,
                            (const ClCtx<SI>*)(cl_ctx + stage), act, b, out);
             AAO_LAUNCH_CHECK();
             return AAO_OK;
@@ -835,54 +872,144 @@ class Precond : public PrecondBase {
         return AAO_OK;
     }
 
-    // Capture one step into a CUDA graph (on a private stream) the first time
+    // A batched step of the recurrence over MGRIT's mg_nc intervals (items b = 0..nc-1 at time
+    // indices sp->n +- b mg_m), or with `residual` the C-point residuals into the coarse source.
+    aao_status schur_step_b(int transpose, int residual) {
+        const Geo& g = h->g;
+        const int s = h->s;
+        const int B = mg_nc, stride = mg_m;
+        const long long item = (long long)s * g.nx;
+        const unsigned nbr = blocks_for_rows(g.R);
+        if (!transpose) {
+            launch(k_schur_rhs_b<A>, dim3(nbr, (unsigned)B), kBlock, 0, st(), g, s, (const StepPtrs*)stepp, stride, tbuf,
+                   sopA);
+            AAO_TRY(inner<A>(B, tbuf, item, nullptr, 0, 0));
+            launch(k_schur_update_b<SI, A>, dim3(nbr, (unsigned)B), kBlock, 0, st(), g, s, (const A*)wbuf,
+                   (const StepPtrs*)stepp, stride, Z0, zstride, (const double*)yh, kin, (const int*)itsh,
+                   (const double*)h->d_b, h->tau, residual ? coarse->wbuf : (A*)nullptr);
+            launch(k_step_add, 1, 1, 0, st(), stepp, 1);
+        } else {
+            launch(k_schurT_rhs_b<A>, dim3((unsigned)((item + 255) / 256), (unsigned)B), 256, 0, st(), g.nx, s,
+                   (const StepPtrs*)stepp, stride, (const double*)h->d_b, tbuf);
+            AAO_TRY(inner<A>(B, tbuf, item, nullptr, 0, 1));
+            const PtMap pm = ptmap(g.n0);
+            Vec<SI> Zc = Z0;
+            launch(k_combine<SI, A>, pt_grid(pm, (long long)s * g.R, B), pt_block(pm), 0, st(), pm, s * g.R, B, Zc,
+                   zstride, (const double*)yh, kin, (const int*)itsh, qbuf, item, 0);
+            launch(k_schurT_update_b<A>, dim3(nbr, (unsigned)B), kBlock, 0, st(), g, s, (const StepPtrs*)stepp, stride,
+                   (const A*)qbuf, h->tau, sopA, residual ? rbufT : (double*)nullptr, B);
+            launch(k_step_add, 1, 1, 0, st(), stepp, -1);
+        }
+        AAO_LAUNCH_CHECK();
+        return AAO_OK;
+    }
+
+    aao_status step_of_kind(int transpose, int kind) {
+        return kind == 0 ? schur_step(transpose) : schur_step_b(transpose, kind == 2);
+    }
+
+    // Capture one step of a kind into a CUDA graph (on a private stream) the first time
     // it is needed; replays then issue the whole step with one launch.
-    aao_status ensure_graph(int transpose) {
-        if (gexec[transpose]) return AAO_OK;
+    aao_status ensure_graph(int transpose, int kind) {
+        if (gexec[transpose][kind]) return AAO_OK;
         if (!cap_stream) AAO_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
         cudaStream_t keep = cur_stream;
         cur_stream = cap_stream;
         const long long before = g_thread_launches;
         AAO_CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
-        aao_status st_ = schur_step(transpose);
+        aao_status st_ = step_of_kind(transpose, kind);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
         cur_stream = keep;
         // captured launches run only when the graph is replayed: count them there
         g_launches -= g_thread_launches - before;
         g_thread_launches = before;
-        if (st_ != AAO_OK) return st_;
+        if (st_ != AAO_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st_;
+        }
         if (e != cudaSuccess) {
             set_error(std::string("graph capture failed: ") + cudaGetErrorString(e));
             return AAO_ERR_CUDA;
         }
         size_t nodes = 0;
         cudaGraphGetNodes(graph, nullptr, &nodes);
-        graph_nodes[transpose] = (long long)nodes;
-        e = cudaGraphInstantiate(&gexec[transpose], graph, 0);
+        graph_nodes[transpose][kind] = (long long)nodes;
+        e = cudaGraphInstantiate(&gexec[transpose][kind], graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
-            gexec[transpose] = nullptr;
+            gexec[transpose][kind] = nullptr;
             set_error(std::string("graph instantiation failed: ") + cudaGetErrorString(e));
             return AAO_ERR_CUDA;
         }
         return AAO_OK;
     }
 
-    aao_status schur_sweep(int transpose) {
-        const int nt = h->nt;
-        // launch profiles need one event pair per kernel: run eagerly then
+    // `count` steps of a kind, each a graph replay (eager launches while a launch profile is open,
+    // which needs one event pair per kernel).
+    aao_status run_steps(int transpose, int kind, int count) {
         const bool use_graph = !g_prof_on;
-        if (use_graph) AAO_TRY(ensure_graph(transpose));
-        for (int q = 0; q < nt; ++q) {
+        if (use_graph) AAO_TRY(ensure_graph(transpose, kind));
+        for (int q = 0; q < count; ++q) {
             if (use_graph) {
-                AAO_CUDA_TRY(cudaGraphLaunch(gexec[transpose], st()));
-                g_launches += graph_nodes[transpose];
+                AAO_CUDA_TRY(cudaGraphLaunch(gexec[transpose][kind], st()));
+                g_launches += graph_nodes[transpose][kind];
             } else {
-                AAO_TRY(schur_step(transpose));
+                AAO_TRY(step_of_kind(transpose, kind));
             }
         }
         return AAO_OK;
+    }
+
+    aao_status schur_sweep(int transpose) { return run_steps(transpose, 0, h->nt); }
+
+    // S_tilde's recurrence z_0 = w_0, z_{n+1} = Phi(z_n) + w_{n+1} by one two-level MGRIT
+    // iteration (C-points n = c m): F-relaxation from z_0 = w_0 and zero C-points, the C-point
+    // residuals, the coarse error recurrence e_c = Phi_c(e_{c-1}) + r_c by substitution with step
+    // m tau, the C-point correction z_{cm} += e_c and a final F-relaxation.  w is in wbuf; z_0
+    // is set by the caller.
+    aao_status mgrit_forward(double* z) {
+        const long long nx = h->g.nx;
+        const int m = mg_m, nc = mg_nc;
+        const unsigned nb = (unsigned)(((long long)nc * nx + 255) / 256);
+        launch(k_mgrit_cpoints, nb, 256, 0, st(), z, (const double*)nullptr, nx, nc, m, 0, 1, 0, 1);
+        launch(k_step_set, 1, 1, 0, st(), stepp, z, (const double*)nullptr, 0);
+        AAO_LAUNCH_CHECK();
+        AAO_TRY(run_steps(0, 1, m - 1));
+        launch(k_step_set, 1, 1, 0, st(), stepp, z, (const double*)nullptr, m - 1);
+        AAO_TRY(run_steps(0, 2, 1));
+        AAO_CUDA_TRY(cudaMemsetAsync(coarse->wbuf, 0, sizeof(A) * nx, st()));
+        AAO_CUDA_TRY(cudaMemsetAsync(ebuf, 0, sizeof(double) * nx, st()));
+        launch(k_step_set, 1, 1, 0, st(), coarse->stepp, ebuf, (const double*)nullptr, 0);
+        AAO_LAUNCH_CHECK();
+        AAO_TRY(coarse->run_steps(0, 0, nc));
+        launch(k_mgrit_cpoints, nb, 256, 0, st(), z, (const double*)ebuf, nx, nc, m, 0, 1, 0, 1);
+        launch(k_step_set, 1, 1, 0, st(), stepp, z, (const double*)nullptr, 0);
+        AAO_LAUNCH_CHECK();
+        return run_steps(0, 1, m - 1);
+    }
+
+    // The same for S_tilde^T's backward recurrence u_nt = r_{v,nt}, u_n = Phi^T(u_{n+1}) + r_{v,n},
+    // run forward in reversed time (C-points n = nt - c m).  u_nt is set by the caller.
+    aao_status mgrit_transpose(double* z, const double* r) {
+        const long long nx = h->g.nx;
+        const int m = mg_m, nc = mg_nc, nt = h->nt;
+        const unsigned nb = (unsigned)(((long long)nc * nx + 255) / 256);
+        launch(k_mgrit_cpoints, nb, 256, 0, st(), z, (const double*)nullptr, nx, nc, m, nt, -1, 0, 1);
+        launch(k_step_set, 1, 1, 0, st(), stepp, z, r, nt - 1);
+        AAO_LAUNCH_CHECK();
+        AAO_TRY(run_steps(1, 1, m - 1));
+        launch(k_step_set, 1, 1, 0, st(), stepp, z, r, nt - m);
+        AAO_TRY(run_steps(1, 2, 1));
+        AAO_CUDA_TRY(cudaMemsetAsync(rbufT + (long long)nc * nx, 0, sizeof(double) * nx, st()));
+        AAO_CUDA_TRY(cudaMemsetAsync(ebuf + (long long)nc * nx, 0, sizeof(double) * nx, st()));
+        launch(k_step_set, 1, 1, 0, st(), coarse->stepp, ebuf, (const double*)rbufT, nc - 1);
+        AAO_LAUNCH_CHECK();
+        AAO_TRY(coarse->run_steps(1, 0, nc));
+        launch(k_mgrit_cpoints, nb, 256, 0, st(), z, (const double*)ebuf, nx, nc, m, nt, -1, nc, -1);
+        launch(k_step_set, 1, 1, 0, st(), stepp, z, r, nt - 1);
+        AAO_LAUNCH_CHECK();
+        return run_steps(1, 1, m - 1);
     }
 
     aao_status apply(const double* r, double* z, int transpose) override {
@@ -912,7 +1039,7 @@ class Precond : public PrecondBase {
             AAO_LAUNCH_CHECK();
             {
                 NvtxRange range_("aao.precond.schur_sweep");
-                AAO_TRY(schur_sweep(0));
+                AAO_TRY(mg_m > 0 ? mgrit_forward(z) : schur_sweep(0));
             }
             cudaEventRecord(e2, st());
         } else {
@@ -923,7 +1050,7 @@ class Precond : public PrecondBase {
             AAO_LAUNCH_CHECK();
             {
                 NvtxRange range_("aao.precond.schur_sweep_transposed");
-                AAO_TRY(schur_sweep(1));
+                AAO_TRY(mg_m > 0 ? mgrit_transpose(z, r) : schur_sweep(1));
             }
             cudaEventRecord(e1, st());
             long long tot = (long long)nt * item;
@@ -1008,15 +1135,18 @@ class Precond : public PrecondBase {
         long long v = 0;
         cudaMemcpyAsync(&v, itcount, sizeof(long long), cudaMemcpyDeviceToHost, st());
         cudaStreamSynchronize(st());
-        return v;
+        return v + (coarse ? coarse->inner_its() : 0);
     }
-    void reset_inner_its() override { cudaMemsetAsync(itcount, 0, sizeof(long long), st()); }
+    void reset_inner_its() override {
+        cudaMemsetAsync(itcount, 0, sizeof(long long), st());
+        if (coarse) coarse->reset_inner_its();
+    }
 
     int nonfinite_flag() override {
         int v[2] = {0, 0};
         cudaMemcpyAsync(v, nonfin, 2 * sizeof(int), cudaMemcpyDeviceToHost, st());
         cudaStreamSynchronize(st());
-        return v[0] | v[1];
+        return v[0] | v[1] | (coarse ? coarse->nonfinite_flag() : 0);
     }
 };
 

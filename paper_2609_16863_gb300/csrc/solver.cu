@@ -261,6 +261,10 @@ static aao_status validate(const aao_grid* grid, double tau, int nt, const aao_t
         set_error("a 16-bit P_tilde needs the same 16-bit P_int");
         return AAO_ERR_ARG;
     }
+    if (o->mgrit_m < 0 || o->mgrit_m == 1 || (o->mgrit_m > 0 && nt % o->mgrit_m != 0)) {
+        set_error("mgrit_m must be 0 (substitution) or a divisor m >= 2 of nt");
+        return AAO_ERR_ARG;
+    }
     if (o->ckpt_every != 0) {
         set_error("ckpt_every must be 0: checkpointed gradients are summed by the caller over windows "
                   "(aao_rk_grad_kappa with accumulate)");
@@ -653,6 +657,7 @@ void aao_rk_default_options(aao_options* o) {
     o->prec_Pint = AAO_FP64;
     o->ckpt_every = 0;
     o->stream = nullptr;
+    o->mgrit_m = 0;
 }
 
 const char* aao_rk_last_error(void) { return get_error(); }
@@ -769,8 +774,8 @@ aao_status aao_rk_set_options(aao_rk_handle hh, const aao_options* o) {
     const aao_options& c = hh->h.opt;
     if (o->prec_P != c.prec_P || o->prec_Pint != c.prec_Pint || o->mg_cycles != c.mg_cycles ||
         o->mg_pre != c.mg_pre || o->mg_post != c.mg_post || o->restart > c.restart || o->restart < 1 ||
-        (o->inner_maxit != 0 && o->inner_maxit != c.inner_maxit)) {
-        set_error("precisions, multigrid shape, inner_maxit and a larger restart are fixed at set-up");
+        (o->inner_maxit != 0 && o->inner_maxit != c.inner_maxit) || o->mgrit_m != c.mgrit_m) {
+        set_error("precisions, multigrid shape, inner_maxit, mgrit_m and a larger restart are fixed at set-up");
         return AAO_ERR_ARG;
     }
     aao_options n = *o;

@@ -1,12 +1,13 @@
-"""Full-size checks at the configuration the benchmark times.
+"""Full-size checks at the configurations the benchmark times.
 
 * 256x256, Radau IIA s=3, 128 steps: the FP64 matvec element by element against the
   oracle (33.6M unknowns), and the FP32-preconditioned solve checked with the
-  oracle's own matvec (true residual <= 1e-8) and against the FP64-preconditioned
-  GPU solve.
+  oracle's own matvec (true residual <= 1e-8) and against the exact all-at-once
+  solution (oracle.spectral, mode by mode in the sine basis) to 1e-8.
 * 96^3, Gauss s=2 / Radau s=3, 32 steps: matvec on sampled time blocks computed by
   the oracle's operators one block at a time; BF16 / FP16 preconditioned solves
-  checked by the oracle's matvec (true residual <= 1e-8).
+  checked by the oracle's matvec (true residual <= 1e-8) and against the exact
+  solution to 1e-8.
 """
 import numpy as np
 import pytest
@@ -42,11 +43,17 @@ def test_fd2d_256_matvec_full_and_fp32_solve():
     xs = host(xs)
     rhs = op.rhs(w.u0, w.f)
     assert info.converged and _true_residual(op, xs, rhs) <= 1e-8
-    S64 = _solver(w, "fp64")
-    x64, i64 = S64.solve(to_dev(w.f), to_dev(w.u0), zeros(op.n_st))
-    err = np.linalg.norm(xs - host(x64)) / np.linalg.norm(host(x64))
-    print(f"fp32 its {info.outer_its} fp64 its {i64.outer_its} rel diff {err:.2e}")
-    assert err <= 1e-7
+    exact = _exact(w, op, rhs)
+    err = np.linalg.norm(xs - exact) / np.linalg.norm(exact)
+    print(f"fp32: outer its {info.outer_its}, error vs the exact solution {err:.2e}")
+    assert err <= 1e-8
+
+
+def _exact(w, op, rhs):
+    from oracle import spectral
+    from oracle.tableau import tableau
+    A, b, _ = tableau(w.method, w.s)
+    return spectral.solve(w.n, op.tau, w.nt, A, b, rhs)
 
 
 def _sampled_matvec_blocks(op, x, blocks):
@@ -79,12 +86,20 @@ def test_fd3d_96_matvec_sampled(method, s):
         assert rel_max(got, ref) <= 1e-13, key
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_fd3d_96_lowprec_solve_residual(prec):
-    w = synth.workload_lowprec_3d(method="radau", s=3)
+@pytest.mark.parametrize("method,s", [("gauss", 2), ("radau", 3)])
+def test_fd3d_96_lowprec_solves_against_exact_solution(method, s):
+    w = synth.workload_lowprec_3d(method=method, s=s)
     op = build(w.n, w.T, w.nt, w.method, w.s)
-    S = _solver(w, prec, inner_maxit=3, inner_tol=1e-3)
-    xs, info = S.solve(to_dev(w.f), to_dev(w.u0), zeros(op.n_st))
-    print(f"{prec}: outer its {info.outer_its} rel_res {info.rel_res:.2e}")
-    assert info.converged
-    assert _true_residual(op, host(xs), op.rhs(w.u0, w.f)) <= 1e-8
+    rhs = op.rhs(w.u0, w.f)
+    exact = _exact(w, op, rhs)
+    for prec in ("bf16", "fp16"):
+        S = _solver(w, prec, inner_maxit=3, inner_tol=1e-3)
+        xs, info = S.solve(to_dev(w.f), to_dev(w.u0), zeros(op.n_st))
+        xs = host(xs)
+        S.close()
+        err = np.linalg.norm(xs - exact) / np.linalg.norm(exact)
+        print(f"{method}{s} {prec}: outer its {info.outer_its} rel_res {info.rel_res:.2e} "
+              f"error vs the exact solution {err:.2e}")
+        assert info.converged
+        assert _true_residual(op, xs, rhs) <= 1e-8
+        assert err <= 1e-8

@@ -213,7 +213,7 @@ def test_mixed_precision_solve_error(prec):
     err = np.linalg.norm(host(x) - ref.x) / np.linalg.norm(ref.x)
     print(f"{prec}: outer {info.outer_its} rel_res {info.rel_res:.2e} err vs FP64 oracle {err:.2e}")
     assert info.converged and info.rel_res <= 1e-8
-    assert err <= 1e-7
+    assert err <= 1e-8
 
 
 # Grids large enough that the fine levels run level by level and only the coarse
@@ -340,5 +340,7 @@ def test_lowprec_solve_ragged(ns, prec):
     f = synth.random_vector(op.nx, 8)
     x, info = S.solve(to_dev(f), to_dev(u0), zeros(op.n_st))
     ref = oracle_solve(op, ns, op.rhs(u0, f), OracleOptions(tol=1e-13))
+    err = np.linalg.norm(host(x) - ref.x) / np.linalg.norm(ref.x)
+    print(f"{ns} {prec}: outer {info.outer_its} err vs FP64 oracle {err:.2e}")
     assert info.converged
-    assert np.linalg.norm(host(x) - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+    assert err <= 1e-8
