@@ -26,7 +26,9 @@ def test_reference_arm_json_line():
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["higher_is_better"] is False and d["value"] > 0
-    assert d["unit"] == "s" and abs(d["ms_per_step"] - 1e3 * d["value"]) < 1e-6 * d["ms_per_step"]
+    # ms_per_step is the measured wall time of a step's bounded sample; value is the time to solution
+    # estimated from it (stated in the config)
+    assert d["unit"] == "s" and 0 < d["ms_per_step"] < 60e3 and d["config"]["value_is_estimate"] is True
     assert "workload" in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] > 0 and cb["value"] == d["value"] and "64x64" in cb["sample"]

@@ -161,3 +161,12 @@ def test_lowprec_preconditioner_within_roundoff_of_fp64(fmtP, fmtI, bound):
     r = synth.random_vector(op.n_st, 10)
     for got, ref in ((E.apply(r), P.apply(r)), (E.apply_T(r), P.apply_T(r))):
         assert np.linalg.norm(got - ref) <= bound * np.linalg.norm(ref)
+
+
+def test_unscaled_fp16_storage_overflows_where_scaled_storage_does_not():
+    """Why 16-bit rows carry a scale: a right-hand side of size 1e7 (and the stiff problem's
+    K-sized intermediates, 4/h^2 ~ 2.6e5 at 256^2) exceed FP16's largest value 65504."""
+    x = (1e7 * synth.random_vector(256, 8)).astype(np.float32)
+    assert np.isinf(lp.round_fp16(x)).any()
+    y = lp.store_rows(x, 64, "fp16")
+    assert np.all(np.isfinite(y)) and np.abs(y - x).max() <= 2.0 ** -11 * np.abs(x).max()
