@@ -37,6 +37,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# MGRIT's dataflow schedule (shifted solves without a cluster plan, e.g. the FP64 arm) runs up to 16
+# worker streams plus the solver's own: give each its hardware queue (set before CUDA starts)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "time-to-1e-8 residual, mixed vs FP64 precond, same GB300; precond HBM GB/s"
 WORKLOAD = "fd2d_n256_radau3_nt128"
@@ -54,7 +57,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--small", action="store_true", help="64x64, nt 16 (quick check; not a bench value)")
     p.add_argument("--workload", default="fd2d_n256_radau3_nt128",
-                   choices=["fd2d_n256_radau3_nt128", "fd3d_n96_radau3_nt32", "fd3d_n96_gauss2_nt32", "batched64"],
+                   choices=["fd2d_n256_radau3_nt128", "fd3d_n96_radau3_nt32", "fd3d_n96_gauss2_nt32", "batched64",
+                            "adjoint_fd2d_n128_kappa_nt64"],
                    help="extra configurations (the default is the benchmark line)")
     p.add_argument("--precond-case", action="store_true",
                    help="small case for profiler captures: --steps applications of P_tilde (FP32) on the "
@@ -118,6 +122,54 @@ def batched_arm(args):
             "dofs_its_per_s": sum(S.n_st * i for S, i in zip(solvers, its)) / t,
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "outer_its_min_max": [min(its), max(its)], "all_converged": all(i.converged for i in infos)}
+    print(json.dumps(line), flush=True)
+
+
+def adjoint_arm(args):
+    """Gradient of J = 1/2 ||u(T) - u_target||^2 + 1/2 1e-4 ||f||^2 with respect to f and the nodal
+    kappa on the 128x128, Radau IIA s=3, 64-step variable-diffusivity workload through the
+    torch.autograd.Function: forward solve keeping states every 8 steps, adjoint solve with
+    P_tilde^T, window-by-window recomputation for the kappa gradient.  One step = forward +
+    backward."""
+    import torch
+    import synth
+    from paper_2609_16863_gb300 import radau_iia
+    from paper_2609_16863_gb300.autograd import heat_solve
+    dev = torch.device("cuda", 0)
+    w = synth.workload_adjoint_2d()
+    mg_m = args.mgrit_m if w.nt % max(args.mgrit_m, 1) == 0 else 0
+    cfg = dict(n=w.n, T=w.T, nt=w.nt, tableau=radau_iia(w.s), prec_P=args.prec, tol=1e-9, maxit=200, ckpt_every=8,
+               inner_maxit=3, inner_tol=1e-3, mgrit_m=mg_m)
+    lo = w.nt * w.nx
+    f0 = torch.from_numpy(w.f).to(dev)
+    u0 = torch.from_numpy(w.u0).to(dev)
+    k0 = torch.from_numpy(w.kappa).to(dev)
+    tg = torch.from_numpy(w.target).to(dev)
+
+    def step():
+        fd = f0.clone().requires_grad_(True)
+        kd = k0.clone().requires_grad_(True)
+        x = heat_solve(fd, u0, kd, **cfg)
+        J = 0.5 * ((x[lo: lo + w.nx] - tg) ** 2).sum() + 0.5e-4 * (fd ** 2).sum()
+        J.backward()
+        return fd.grad, kd.grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        gf, gk = step()
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / args.steps
+    line = {"metric": "gradient (forward + adjoint with checkpoints every 8 steps) wall time", "value": t, "unit": "s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": f"f64/{args.prec}",
+            "data": "synthetic",
+            "config": {"workload": "adjoint_fd2d_n128_kappa_nt64", "n_st": w.nx * (w.nt + 1 + w.s * w.nt),
+                       "schur": f"MGRIT m = {mg_m}" if mg_m else "forward substitution",
+                       "checkpoints": "every 8 steps", "tol": 1e-9},
+            "grad_norms": {"f": float(torch.linalg.norm(gf)), "kappa": float(torch.linalg.norm(gk))}}
     print(json.dumps(line), flush=True)
 
 
@@ -418,6 +470,9 @@ def main():
         return
     if args.workload == "batched64":
         batched_arm(args)
+        return
+    if args.workload == "adjoint_fd2d_n128_kappa_nt64":
+        adjoint_arm(args)
         return
     if args.precond_case:
         precond_case(args)

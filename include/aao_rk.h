@@ -10,7 +10,7 @@
  *     [ Phi    Psi_1 ] [ v ]   [ b ]
  *     [ Psi_2  Theta ] [ V ] = [ f ],
  *
- * solved by restarted flexible GMRES in FP64 (Algorithm 1, P_L = I) with the
+ * solved by restarted flexible GMRES in FP64 (Algorithm 1, P_L = I, or P_R = I) with the
  * block-triangular preconditioner P_tilde of Eq. (AppPrec): Theta_tilde by
  * inner GMRES on Theta_hat preconditioned by Rana's stage sweep (block LDU of
  * A_RK) with multigrid V-cycles for M + tau d_i K, and the Schur approximation
@@ -111,6 +111,11 @@ typedef struct {
                           * factor m and F-relaxation, the coarse step being the same substitution
                           * step with step size m tau (the parallel implementation of Sec. 5);
                           * P_tilde^T runs it on the backward recurrence in reversed time */
+    int precond_side;    /* 0: right preconditioning, FGMRES with P_R = P_tilde (Algorithm 1 with
+                          * P_L = I; the sequential runs of Sec. 5.1); 1: left preconditioning,
+                          * P_L = P_tilde and P_R = I (Algorithm 1; the parallel runs of Sec. 5.2),
+                          * converged when ||P^{-1} b - P^{-1} A x|| <= tol ||P^{-1} b||, with
+                          * rel_res still the true ||b - A x|| / ||b|| */
 } aao_options;
 
 typedef struct {
@@ -156,8 +161,8 @@ const char* aao_rk_profile_report(void);
 /* n_x = prod(n), n_st = n_x (nt + 1 + s nt). */
 aao_status aao_rk_sizes(aao_rk_handle h, long long* n_x, long long* n_st);
 /* Replace tol / restart / maxit / inner_tol (precisions, multigrid shape,
- * inner_maxit, mgrit_m and the stream are fixed at set-up; changing them
- * returns AAO_ERR_ARG). */
+ * inner_maxit, mgrit_m, precond_side and the stream are fixed at set-up;
+ * changing them returns AAO_ERR_ARG). */
 aao_status aao_rk_set_options(aao_rk_handle h, const aao_options* opts);
 
 /* rhs = [M u0 ; 0 .. 0 ; M f_{n,i}] (Sec. 2 with zero Dirichlet data).  f has

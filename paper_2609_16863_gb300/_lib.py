@@ -34,7 +34,7 @@ class aao_options(C.Structure):
                 ("mg_cycles", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
                 ("mg_omega", C.c_double), ("cheb_steps", C.c_int),
                 ("prec_P", C.c_int), ("prec_Pint", C.c_int), ("ckpt_every", C.c_int),
-                ("stream", C.c_void_p), ("mgrit_m", C.c_int)]
+                ("stream", C.c_void_p), ("mgrit_m", C.c_int), ("precond_side", C.c_int)]
 
 
 class aao_info(C.Structure):

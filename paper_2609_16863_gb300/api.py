@@ -60,13 +60,15 @@ class Solver:
     """Handle for one problem: grid n (interior points per axis), final time T,
     nt steps, an RK tableau (A, b, c), optional nodal diffusivity kappa.  mgrit_m > 0
     (a divisor of nt) replaces S_tilde's forward substitution by one two-level MGRIT
-    iteration with coarsening factor mgrit_m."""
+    iteration with coarsening factor mgrit_m; precond_side="left" runs Algorithm 1 with
+    P_L = P_tilde, P_R = I instead of the right-preconditioned FGMRES."""
 
     def __init__(self, n: Sequence[int], T: float, nt: int, tableau=None, method: str = "radau", s: int = 2,
                  lens=None, kappa=None, prec_P: str = "fp64", prec_Pint: Optional[str] = None,
                  tol: float = 1e-8, restart: int = 20, maxit: int = 100, inner_maxit: int = 0,
                  inner_tol: float = -1.0, mg_cycles: int = 3, mg_pre: int = 2, mg_post: int = 2,
-                 mg_omega: float = 0.8, disc: str = "fd", cheb_steps: int = 20, stream=None, mgrit_m: int = 0):
+                 mg_omega: float = 0.8, disc: str = "fd", cheb_steps: int = 20, stream=None, mgrit_m: int = 0,
+                 precond_side: str = "right"):
         self._lib = _lib.lib()
         self.n = tuple(int(v) for v in n)
         self.dim = len(self.n)
@@ -101,6 +103,7 @@ class Solver:
         o.prec_Pint = _lib.PREC[prec_Pint if prec_Pint is not None else prec_P]
         o.stream = stream
         o.mgrit_m = mgrit_m
+        o.precond_side = {"right": 0, "left": 1}[precond_side]
         self.options = o
         h = C.c_void_p()
         _lib.check(self._lib.aao_rk_setup(C.byref(g), self.tau, self.nt, C.byref(t), C.byref(o), C.byref(h)))

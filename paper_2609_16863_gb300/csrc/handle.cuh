@@ -117,7 +117,8 @@ struct Handle {
     // outer FGMRES workspace
     int m = 0;                     // restart
     double* V = nullptr;           // (m+1) * nst
-    double* Z = nullptr;           // m * nst
+    double* Z = nullptr;           // m * nst (right preconditioning)
+    double* bt = nullptr;          // nst: P^{-1} b (left preconditioning)
     double* w = nullptr;           // nst
     double* r = nullptr;           // nst
     double* rhs = nullptr;         // nst (staging for solve / host inputs)

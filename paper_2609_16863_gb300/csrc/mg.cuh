@@ -358,6 +358,121 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_smooth_rows(LevelOp<S> op, Pt
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched 2D matrix-free level (sigma I + c K, kappa = 1), unscaled storage, streaming form:
+// a thread owns V consecutive columns (one 16-byte vector) of a strip of RS rows and keeps the
+// rows j-1, j, j+1 of x in registers while it walks down the strip, so each point costs one
+// vector load of x, one of b and one store (plus two scalar halo loads per row and two halo
+// rows per strip).  MODE 0: damped Jacobi x + omega (b - A x) / a_PP; MODE 1: the same from
+// x = 0 (omega b / a_PP, x is not read); MODE 2: the residual b - A x.  Same arithmetic as
+// level_apply_k<4>.  Block: 256 threads = (n0 / V) threads per row x strips; grid
+// (ceil(n1 / (strips RS)), items).
+// ---------------------------------------------------------------------------
+template <class S> struct Vec16;
+template <> struct Vec16<float> {
+    using T = float4;
+    static constexpr int n = 4;
+};
+template <> struct Vec16<double> {
+    using T = double2;
+    static constexpr int n = 2;
+};
+constexpr int kStripThreads = 256;
+constexpr int kStripRows = 8;
+
+template <class S, int MODE>
+__global__ void __launch_bounds__(kStripThreads) k_strip2d(LevelOp<S> op, int B, const int* active, Vec<S> xin,
+                                                           Vec<S> bv, Vec<S> out, S omega) {
+    pdl_prologue();
+    static_assert(!PT<S>::scaled, "unscaled storage only");
+    using VT = typename Vec16<S>::T;
+    constexpr int V = Vec16<S>::n;
+    const Geo g = op.g;
+    const int b = blockIdx.y;
+    if (b >= B || (active && !active[b])) return;
+    const int n0 = g.n0, n1 = g.n1;
+    const int tpr = n0 / V;
+    const int tx = threadIdx.x % tpr, ty = threadIdx.x / tpr;
+    const int strips = blockDim.x / tpr;
+    if (ty >= strips) return;
+    const int j0 = (blockIdx.x * strips + ty) * kStripRows;
+    if (j0 >= n1) return;
+    const int j1 = j0 + kStripRows < n1 ? j0 + kStripRows : n1;
+    const int c0 = tx * V;
+    const S* X = MODE == 1 ? nullptr : xin.d + (long long)b * xin.bs;
+    const S* Bp = bv.d + (long long)b * bv.bs;
+    S* O = out.d + (long long)b * out.bs;
+    const S hx2 = S(g.hx2), hy2 = S(g.hy2);
+    const S kd = S(2) * hx2 + S(2) * hy2;
+    const S dg = op.sigma + op.c * kd;
+    S sr[V], pr[V], nr[V];
+    auto load_row = [&](int j, S* dst) {
+        if (j >= 0 && j < n1) {
+            VT v = *reinterpret_cast<const VT*>(X + (long long)j * n0 + c0);
+            const S* q = reinterpret_cast<const S*>(&v);
+#pragma unroll
+            for (int t = 0; t < V; ++t) dst[t] = q[t];
+        } else {
+#pragma unroll
+            for (int t = 0; t < V; ++t) dst[t] = S(0);
+        }
+    };
+    if (MODE != 1) {
+        load_row(j0 - 1, sr);
+        load_row(j0, pr);
+    }
+    for (int j = j0; j < j1; ++j) {
+        const VT bvec = *reinterpret_cast<const VT*>(Bp + (long long)j * n0 + c0);
+        const S* bq = reinterpret_cast<const S*>(&bvec);
+        S res[V];
+        if (MODE == 1) {
+#pragma unroll
+            for (int t = 0; t < V; ++t) res[t] = omega * bq[t] / dg;
+        } else {
+            load_row(j + 1, nr);
+            const S w = c0 > 0 ? X[(long long)j * n0 + c0 - 1] : S(0);
+            const S e = c0 + V < n0 ? X[(long long)j * n0 + c0 + V] : S(0);
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                const S uP = pr[t], uW = t == 0 ? w : pr[t - 1], uE = t == V - 1 ? e : pr[t + 1];
+                const S K = hx2 * (S(2) * uP - uW - uE) + hy2 * (S(2) * uP - sr[t] - nr[t]);
+                const S Au = op.sigma * uP + op.c * K;
+                res[t] = MODE == 0 ? uP + omega * (bq[t] - Au) / dg : bq[t] - Au;
+            }
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                sr[t] = pr[t];
+                pr[t] = nr[t];
+            }
+        }
+        VT ov;
+        S* oq = reinterpret_cast<S*>(&ov);
+#pragma unroll
+        for (int t = 0; t < V; ++t) oq[t] = res[t];
+        *reinterpret_cast<VT*>(O + (long long)j * n0 + c0) = ov;
+    }
+}
+
+// Whether a level takes k_strip2d: 2D matrix-free with kappa = 1, unscaled storage, rows of whole
+// 16-byte vectors that tile a 256-thread block, and 16-byte aligned rows.
+template <class S>
+inline bool strip_ok(const LevelOp<S>& op) {
+    if constexpr (PT<S>::scaled) {
+        return false;
+    } else {
+        constexpr int V = Vec16<S>::n;
+        const int n0 = op.g.n0;
+        return op.fine && op.g.d == 2 && op.faces.fx == nullptr && n0 % V == 0 && n0 / V <= kStripThreads &&
+               kStripThreads % (n0 / V) == 0;
+    }
+}
+template <class S>
+inline dim3 strip_grid(const LevelOp<S>& op, int B) {
+    const int tpr = op.g.n0 / Vec16<S>::n;
+    const int rows_per_block = (kStripThreads / tpr) * kStripRows;
+    return dim3((unsigned)((op.g.n1 + rows_per_block - 1) / rows_per_block), (unsigned)B, 1);
+}
+
 // r = b - A x for unscaled storage, RPT rows per thread (as k_smooth_rows).
 template <class S, int KIND, int RPT>
 __global__ void __launch_bounds__(kPtMaxThreads) k_residual_rows(LevelOp<S> op, PtMap pm, int B, const int* active,

@@ -98,6 +98,17 @@ class Precond : public PrecondBase {
     Precond* coarse = nullptr;
     double* ebuf = nullptr;        // (nc+1)*nx: coarse error recurrence
     double* rbufT = nullptr;       // (nc+1)*nx: transposed C-point residuals (the coarse source)
+    // The intervals' recurrences run as single-item steps on worker preconditioners (same
+    // operators, one stream each, their own Krylov and reduction workspace; they read this
+    // preconditioner's w), ordered by events: the dataflow of one two-level MGRIT iteration.
+    static constexpr int kMaxWorkers = 16;
+    int nwork = 0;
+    std::unique_ptr<Handle> hw[kMaxWorkers];
+    Precond* work[kMaxWorkers] = {};
+    cudaStream_t wst[kMaxWorkers] = {};
+    cudaEvent_t ev_start = nullptr, ev_join[kMaxWorkers] = {};
+    std::vector<cudaEvent_t> ev_f1, ev_c;    // per interval: first relaxation done, C-point corrected
+    const A* wsrc = nullptr;       // a worker's source w (the owner's wbuf); nullptr: its own
 
     cudaStream_t st() const { return cur_stream; }
 
@@ -129,6 +140,22 @@ class Precond : public PrecondBase {
         if (coarse) delete coarse;
         coarse = nullptr;
         hc.reset();
+        for (int w = 0; w < kMaxWorkers; ++w) {
+            if (work[w]) delete work[w];
+            work[w] = nullptr;
+            hw[w].reset();
+            if (wst[w]) cudaStreamDestroy(wst[w]);
+            wst[w] = nullptr;
+            if (ev_join[w]) cudaEventDestroy(ev_join[w]);
+            ev_join[w] = nullptr;
+        }
+        nwork = 0;
+        for (cudaEvent_t e : ev_f1) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_c) cudaEventDestroy(e);
+        ev_f1.clear();
+        ev_c.clear();
+        if (ev_start) cudaEventDestroy(ev_start);
+        ev_start = nullptr;
         for (int i = 0; i < 2; ++i)
             for (int k = 0; k < 3; ++k) {
                 if (gexec[i][k]) cudaGraphExecDestroy(gexec[i][k]);
@@ -353,6 +380,34 @@ class Precond : public PrecondBase {
             AAO_TRY(coarse->setup());
             AAO_TRY(ar.alloc(&ebuf, (size_t)((mg_nc + 1) * g0.nx)));
             AAO_TRY(ar.alloc(&rbufT, (size_t)((mg_nc + 1) * g0.nx)));
+            // the dataflow schedule needs no clusters: with a cluster plan the lock-step schedule runs
+            nwork = cl_C > 0 ? 0 : std::min(mg_nc, (int)kMaxWorkers);
+            for (int w = 0; w < nwork; ++w) {
+                AAO_CUDA_TRY(cudaStreamCreateWithFlags(&wst[w], cudaStreamNonBlocking));
+                AAO_CUDA_TRY(cudaEventCreateWithFlags(&ev_join[w], cudaEventDisableTiming));
+                hw[w].reset(new Handle(*h));
+                Handle* q = hw[w].get();
+                q->arena = Arena();
+                q->P = nullptr;
+                q->nt = 1;
+                q->nv = 2 * g0.nx;
+                q->nst = q->nv + (long long)s * g0.nx;
+                q->opt.mgrit_m = 0;
+                q->stream = wst[w];
+                // a worker's reductions run concurrently with the others': its own scratch
+                q->red_cap_items = 1;
+                AAO_TRY(ar.alloc(&q->red.partials, (size_t)(q->red_cap_chunks + 1 + 16)));
+                AAO_TRY(ar.alloc(&q->red.count, 1));
+                AAO_CUDA_TRY(cudaMemsetAsync(q->red.count, 0, sizeof(unsigned int), st()));
+                work[w] = new Precond(q);
+                AAO_TRY(work[w]->setup());
+                work[w]->wsrc = wbuf;
+            }
+            ev_f1.assign(mg_nc, nullptr);
+            ev_c.assign(mg_nc + 1, nullptr);
+            for (auto& e : ev_f1) AAO_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            for (auto& e : ev_c) AAO_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            AAO_CUDA_TRY(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming));
         }
         AAO_CUDA_TRY(cudaStreamSynchronize(st()));
         return AAO_OK;
@@ -609,7 +664,19 @@ class Precond : public PrecondBase {
     }
 
     // Smoother and residual launches specialised by level kind (2D matrix-free, 2D stored; 3D generic).
-    template <class... Args> void launch_smooth(int kind, dim3 grid, dim3 block, Args... args) {
+    // Large batches of the 2D matrix-free level (kappa = 1) take the streaming strip kernel.
+    void launch_smooth(int kind, dim3 grid, dim3 block, const LevelOp<SI>& op, const PtMap& pm, int B, const int* act,
+                       Vec<SI> x, Vec<SI> b, Vec<SI> out, A om) {
+        if constexpr (!PT<SI>::scaled) {
+            if (kind == 4 && grid.y >= 16 && strip_ok(op)) {
+                if (x.d) launch(k_strip2d<SI, 0>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, om);
+                else launch(k_strip2d<SI, 1>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, om);
+                return;
+            }
+        }
+        launch_smooth_rows(kind, grid, block, op, pm, B, act, x, b, out, om);
+    }
+    template <class... Args> void launch_smooth_rows(int kind, dim3 grid, dim3 block, Args... args) {
         if constexpr (!PT<SI>::scaled) {
             // large 2D batches: four rows per thread (grid.y = items)
             constexpr int kRows = 4;
@@ -624,7 +691,17 @@ class Precond : public PrecondBase {
         else if (kind == 2) launch(k_smooth<SI, 2>, grid, block, 0, st(), args...);
         else launch(k_smooth<SI, 0>, grid, block, 0, st(), args...);
     }
-    template <class... Args> void launch_residual(int kind, dim3 grid, dim3 block, Args... args) {
+    void launch_residual(int kind, dim3 grid, dim3 block, const LevelOp<SI>& op, const PtMap& pm, int B,
+                         const int* act, Vec<SI> x, Vec<SI> b, Vec<SI> out) {
+        if constexpr (!PT<SI>::scaled) {
+            if (kind == 4 && grid.y >= 16 && strip_ok(op) && x.d) {
+                launch(k_strip2d<SI, 2>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, A(0));
+                return;
+            }
+        }
+        launch_residual_rows(kind, grid, block, op, pm, B, act, x, b, out);
+    }
+    template <class... Args> void launch_residual_rows(int kind, dim3 grid, dim3 block, Args... args) {
         if constexpr (!PT<SI>::scaled) {
             constexpr int kRows = 4;
             if ((kind == 4 || kind == 2) && grid.y >= 16) {
@@ -853,7 +930,8 @@ class Precond : public PrecondBase {
         if (!transpose) {
             launch(k_schur_rhs<A>, nbr, kBlock, 0, st(), g, s, (const StepPtrs*)stepp, tbuf, sopA);
             AAO_TRY(inner<A>(1, tbuf, item, nullptr, 0, 0));
-            launch(k_schur_update<SI, A>, nbr, kBlock, 0, st(), g, s, (const A*)wbuf, (const StepPtrs*)stepp, Z0,
+            launch(k_schur_update<SI, A>, nbr, kBlock, 0, st(), g, s, wsrc ? wsrc : (const A*)wbuf,
+                   (const StepPtrs*)stepp, Z0,
                    zstride, (const double*)yh, kin, (const int*)itsh, (const double*)h->d_b, h->tau);
             launch(k_step_add, 1, 1, 0, st(), stepp, 1);
         } else {
@@ -964,11 +1042,115 @@ class Precond : public PrecondBase {
     aao_status schur_sweep(int transpose) { return run_steps(transpose, 0, h->nt); }
 
     // S_tilde's recurrence z_0 = w_0, z_{n+1} = Phi(z_n) + w_{n+1} by one two-level MGRIT
-    // iteration (C-points n = c m): F-relaxation from z_0 = w_0 and zero C-points, the C-point
+    // iteration with C-points n = c m (F-relaxation; initial guess z_0 = w_0, zero C-points):
+    //   1. interval c relaxes from its C-point to the next one; z_{cm+1} = Phi(0) + w_{cm+1} =
+    //      w_{cm+1} for c > 0, and the interval's last step yields the next C-point's residual
+    //      r_{c+1} = w_{(c+1)m} + Phi(z_{(c+1)m-1}) - 0 in place of that (zero) C-point;
+    //   2. the coarse recurrence e_c = Phi_c(e_{c-1}) + r_c (the substitution step with step m tau),
+    //      and the corrected C-point z_{cm} = 0 + e_c;
+    //   3. a final F-relaxation of every interval from its corrected C-point.
+    // The intervals run on the workers' streams; event c orders interval c's first relaxation before
+    // coarse step c+1, and coarse step c before interval c's final relaxation, so the coarse chain
+    // overlaps the intervals' work.  Used when the shifted solves run as level kernels (no cluster
+    // plan): concurrent single-item steps then fill the GPU.  w is in wbuf; z_0 is set by the caller.
+    aao_status mgrit_dataflow_forward(double* z) {
+        const long long nx = h->g.nx;
+        const int m = mg_m, nc = mg_nc, K = nwork;
+        const unsigned nb = (unsigned)((nx + 255) / 256);
+        AAO_CUDA_TRY(cudaEventRecord(ev_start, st()));
+        for (int w = 0; w < K; ++w) AAO_CUDA_TRY(cudaStreamWaitEvent(wst[w], ev_start, 0));
+        for (int c = 0; c < nc; ++c) {
+            Precond* W = work[c % K];
+            if (c == 0) {
+                launch(k_step_set, 1, 1, 0, W->st(), W->stepp, z, (const double*)nullptr, 0);
+                AAO_TRY(W->run_steps(0, 0, m));
+            } else {
+                launch(k_convert<A, double>, nb, 256, 0, W->st(), (const A*)(wbuf + (long long)(c * m + 1) * nx),
+                       z + (long long)(c * m + 1) * nx, nx);
+                launch(k_step_set, 1, 1, 0, W->st(), W->stepp, z, (const double*)nullptr, c * m + 1);
+                AAO_TRY(W->run_steps(0, 0, m - 1));
+            }
+            AAO_CUDA_TRY(cudaEventRecord(ev_f1[c], W->st()));
+        }
+        AAO_CUDA_TRY(cudaMemsetAsync(coarse->wbuf, 0, sizeof(A) * nx, st()));
+        AAO_CUDA_TRY(cudaMemsetAsync(ebuf, 0, sizeof(double) * nx, st()));
+        launch(k_step_set, 1, 1, 0, st(), coarse->stepp, ebuf, (const double*)nullptr, 0);
+        for (int c = 1; c <= nc; ++c) {
+            AAO_CUDA_TRY(cudaStreamWaitEvent(st(), ev_f1[c - 1], 0));
+            launch(k_convert<double, A>, nb, 256, 0, st(), (const double*)(z + (long long)c * m * nx),
+                   coarse->wbuf + (long long)c * nx, nx);
+            AAO_TRY(coarse->run_steps(0, 0, 1));
+            AAO_CUDA_TRY(cudaMemcpyAsync(z + (long long)c * m * nx, ebuf + (long long)c * nx, sizeof(double) * nx,
+                                         cudaMemcpyDeviceToDevice, st()));
+            AAO_CUDA_TRY(cudaEventRecord(ev_c[c], st()));
+        }
+        for (int c = 0; c < nc; ++c) {
+            Precond* W = work[c % K];
+            if (c > 0) AAO_CUDA_TRY(cudaStreamWaitEvent(W->st(), ev_c[c], 0));
+            launch(k_step_set, 1, 1, 0, W->st(), W->stepp, z, (const double*)nullptr, c * m);
+            AAO_TRY(W->run_steps(0, 0, m - 1));
+        }
+        for (int w = 0; w < K; ++w) {
+            AAO_CUDA_TRY(cudaEventRecord(ev_join[w], wst[w]));
+            AAO_CUDA_TRY(cudaStreamWaitEvent(st(), ev_join[w], 0));
+        }
+        AAO_LAUNCH_CHECK();
+        return AAO_OK;
+    }
+
+    // The same for S_tilde^T's backward recurrence u_nt = r_{v,nt}, u_n = Phi^T(u_{n+1}) + r_{v,n},
+    // run forward in reversed time (C-points n = nt - c m).  u_nt is set by the caller.
+    aao_status mgrit_dataflow_transpose(double* z, const double* r) {
+        const long long nx = h->g.nx;
+        const int m = mg_m, nc = mg_nc, K = nwork, nt = h->nt;
+        AAO_CUDA_TRY(cudaEventRecord(ev_start, st()));
+        for (int w = 0; w < K; ++w) AAO_CUDA_TRY(cudaStreamWaitEvent(wst[w], ev_start, 0));
+        for (int c = 0; c < nc; ++c) {
+            Precond* W = work[c % K];
+            if (c == 0) {
+                launch(k_step_set, 1, 1, 0, W->st(), W->stepp, z, r, nt - 1);
+                AAO_TRY(W->run_steps(1, 0, m));
+            } else {
+                const long long n1 = nt - c * m - 1;
+                AAO_CUDA_TRY(cudaMemcpyAsync(z + n1 * nx, r + n1 * nx, sizeof(double) * nx, cudaMemcpyDeviceToDevice,
+                                             W->st()));
+                launch(k_step_set, 1, 1, 0, W->st(), W->stepp, z, r, (int)n1 - 1);
+                AAO_TRY(W->run_steps(1, 0, m - 1));
+            }
+            AAO_CUDA_TRY(cudaEventRecord(ev_f1[c], W->st()));
+        }
+        AAO_CUDA_TRY(cudaMemsetAsync(rbufT + (long long)nc * nx, 0, sizeof(double) * nx, st()));
+        AAO_CUDA_TRY(cudaMemsetAsync(ebuf + (long long)nc * nx, 0, sizeof(double) * nx, st()));
+        launch(k_step_set, 1, 1, 0, st(), coarse->stepp, ebuf, (const double*)rbufT, nc - 1);
+        for (int c = 1; c <= nc; ++c) {
+            AAO_CUDA_TRY(cudaStreamWaitEvent(st(), ev_f1[c - 1], 0));
+            const long long zc = (long long)(nt - c * m) * nx, ec = (long long)(nc - c) * nx;
+            AAO_CUDA_TRY(cudaMemcpyAsync(rbufT + ec, z + zc, sizeof(double) * nx, cudaMemcpyDeviceToDevice, st()));
+            AAO_TRY(coarse->run_steps(1, 0, 1));
+            AAO_CUDA_TRY(cudaMemcpyAsync(z + zc, ebuf + ec, sizeof(double) * nx, cudaMemcpyDeviceToDevice, st()));
+            AAO_CUDA_TRY(cudaEventRecord(ev_c[c], st()));
+        }
+        for (int c = 0; c < nc; ++c) {
+            Precond* W = work[c % K];
+            if (c > 0) AAO_CUDA_TRY(cudaStreamWaitEvent(W->st(), ev_c[c], 0));
+            launch(k_step_set, 1, 1, 0, W->st(), W->stepp, z, r, nt - c * m - 1);
+            AAO_TRY(W->run_steps(1, 0, m - 1));
+        }
+        for (int w = 0; w < K; ++w) {
+            AAO_CUDA_TRY(cudaEventRecord(ev_join[w], wst[w]));
+            AAO_CUDA_TRY(cudaStreamWaitEvent(st(), ev_join[w], 0));
+        }
+        AAO_LAUNCH_CHECK();
+        return AAO_OK;
+    }
+
+    // Lock-step schedule of the same MGRIT iteration (used when a shifted solve runs on one
+    // thread-block cluster: one launch then holds every interval's clusters): F-relaxation as
+    // batched steps over the mg_nc intervals from z_0 = w_0 and zero C-points, the C-point
     // residuals, the coarse error recurrence e_c = Phi_c(e_{c-1}) + r_c by substitution with step
     // m tau, the C-point correction z_{cm} += e_c and a final F-relaxation.  w is in wbuf; z_0
     // is set by the caller.
-    aao_status mgrit_forward(double* z) {
+    aao_status mgrit_batched_forward(double* z) {
         const long long nx = h->g.nx;
         const int m = mg_m, nc = mg_nc;
         const unsigned nb = (unsigned)(((long long)nc * nx + 255) / 256);
@@ -991,7 +1173,7 @@ class Precond : public PrecondBase {
 
     // The same for S_tilde^T's backward recurrence u_nt = r_{v,nt}, u_n = Phi^T(u_{n+1}) + r_{v,n},
     // run forward in reversed time (C-points n = nt - c m).  u_nt is set by the caller.
-    aao_status mgrit_transpose(double* z, const double* r) {
+    aao_status mgrit_batched_transpose(double* z, const double* r) {
         const long long nx = h->g.nx;
         const int m = mg_m, nc = mg_nc, nt = h->nt;
         const unsigned nb = (unsigned)(((long long)nc * nx + 255) / 256);
@@ -1010,6 +1192,11 @@ class Precond : public PrecondBase {
         launch(k_step_set, 1, 1, 0, st(), stepp, z, r, nt - 1);
         AAO_LAUNCH_CHECK();
         return run_steps(1, 1, m - 1);
+    }
+
+    aao_status mgrit_forward(double* z) { return nwork ? mgrit_dataflow_forward(z) : mgrit_batched_forward(z); }
+    aao_status mgrit_transpose(double* z, const double* r) {
+        return nwork ? mgrit_dataflow_transpose(z, r) : mgrit_batched_transpose(z, r);
     }
 
     aao_status apply(const double* r, double* z, int transpose) override {
@@ -1135,18 +1322,22 @@ class Precond : public PrecondBase {
         long long v = 0;
         cudaMemcpyAsync(&v, itcount, sizeof(long long), cudaMemcpyDeviceToHost, st());
         cudaStreamSynchronize(st());
+        for (int w = 0; w < nwork; ++w) v += work[w]->inner_its();
         return v + (coarse ? coarse->inner_its() : 0);
     }
     void reset_inner_its() override {
         cudaMemsetAsync(itcount, 0, sizeof(long long), st());
         if (coarse) coarse->reset_inner_its();
+        for (int w = 0; w < nwork; ++w) work[w]->reset_inner_its();
     }
 
     int nonfinite_flag() override {
         int v[2] = {0, 0};
         cudaMemcpyAsync(v, nonfin, 2 * sizeof(int), cudaMemcpyDeviceToHost, st());
         cudaStreamSynchronize(st());
-        return v[0] | v[1] | (coarse ? coarse->nonfinite_flag() : 0);
+        int wf = 0;
+        for (int w = 0; w < nwork; ++w) wf |= work[w]->nonfinite_flag();
+        return v[0] | v[1] | wf | (coarse ? coarse->nonfinite_flag() : 0);
     }
 };
 

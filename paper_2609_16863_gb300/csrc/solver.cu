@@ -165,6 +165,13 @@ __global__ void k_outer_init(double* g, int m, const double* beta, int* flags) {
     }
 }
 
+// w = bt - w (the left-preconditioned residual P^{-1} b - P^{-1} A x).
+__global__ void k_sub_from(double* w, const double* bt, long long n) {
+    pdl_prologue();
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] = bt[i] - w[i];
+}
+
 struct SmallDev {
     double resid;
     int active, its, nonfinite, breakdown;
@@ -259,6 +266,10 @@ static aao_status validate(const aao_grid* grid, double tau, int nt, const aao_t
     }
     if ((P == AAO_BF16 || P == AAO_FP16) && I != P) {
         set_error("a 16-bit P_tilde needs the same 16-bit P_int");
+        return AAO_ERR_ARG;
+    }
+    if (o->precond_side != 0 && o->precond_side != 1) {
+        set_error("precond_side must be 0 (right) or 1 (left)");
         return AAO_ERR_ARG;
     }
     if (o->mgrit_m < 0 || o->mgrit_m == 1 || (o->mgrit_m > 0 && nt % o->mgrit_m != 0)) {
@@ -382,7 +393,8 @@ static aao_status setup_handle(Handle* h, const aao_grid* grid, double tau, int 
     h->m = h->opt.restart;
     const int m = h->m;
     AAO_TRY(ar.alloc(&h->V, (size_t)(m + 1) * h->nst));
-    AAO_TRY(ar.alloc(&h->Z, (size_t)m * h->nst));
+    if (h->opt.precond_side == 1) AAO_TRY(ar.alloc(&h->bt, (size_t)h->nst));   // left: P^{-1} b, no Z basis
+    else AAO_TRY(ar.alloc(&h->Z, (size_t)m * h->nst));
     AAO_TRY(ar.alloc(&h->w, (size_t)h->nst));
     AAO_TRY(ar.alloc(&h->r, (size_t)h->nst));
     AAO_TRY(ar.alloc(&h->rhs, (size_t)h->nst));
@@ -583,6 +595,148 @@ static aao_status fgmres(Handle* h, const double* b, double* x, int x0_given, in
     return status;
 }
 
+// Algorithm 1 with P_L = P_tilde (or P_tilde^T) and P_R = I, in FP64 (the left preconditioning of
+// the paper's parallel runs, Sec. 5.2): r_0 = P^{-1} b - P^{-1} A x_0, beta_0 = ||r_0|| of the first
+// cycle; iteration k: w = P^{-1} (A v_k), modified Gram--Schmidt, Givens; a cycle ends when
+// |g_{k+1}| <= tol beta_0, h_{k+1,k} = 0, after `restart` iterations or at maxit; x += V_k y_k;
+// the solve has converged when the recomputed ||P^{-1} b - P^{-1} A x|| <= tol beta_0.  rel_res
+// reports the true ||b - A x|| / ||b||.
+static aao_status fgmres_left(Handle* h, const double* b, double* x, int x0_given, int transpose, aao_info* info,
+                              SmallDev* sd) {
+    NvtxRange range_(transpose ? "aao.fgmres_left_adjoint" : "aao.fgmres_left");
+    auto t0 = std::chrono::steady_clock::now();
+    const long long nst = h->nst;
+    const int n0 = h->g.n0, m = h->m;
+    const long long rows = nst / n0;
+    cudaStream_t st = h->stream;
+    aao_info loc;
+    memset(&loc, 0, sizeof(loc));
+    h->P->t_theta_ms = h->P->t_schur_ms = 0.f;
+    h->P->reset_inner_its();
+    AAO_TRY(norm_dev(h, b, h->beta + 1));
+    double bnorm = 0.0;
+    AAO_CUDA_TRY(cudaMemcpyAsync(&bnorm, h->beta + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    AAO_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!std::isfinite(bnorm)) {
+        set_error("right-hand side is not finite");
+        return AAO_ERR_NONFINITE;
+    }
+    aao_status status = AAO_OK;
+    const unsigned nbl = (unsigned)((nst + 255) / 256);
+    if (bnorm == 0.0) {
+        AAO_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * nst, st));
+        loc.converged = 1;
+    } else {
+        if (!x0_given) AAO_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * nst, st));
+        AAO_TRY(h->P->apply(b, h->bt, transpose));                 // P^{-1} b
+        double beta0 = -1.0, beta = 0.0;
+        int total = 0;
+        const double tol = h->opt.tol;
+        Red red = h->red;
+        red.nchunk = h->nchunk_for(1, rows * ((n0 + kWarp - 1) / kWarp));
+        dim3 rgrid(red.nchunk, 1);
+        const PtMap pmo = ptmap(n0);
+        const dim3 nbp = pt_grid(pmo, rows, 1), ntp = pt_block(pmo);
+        while (true) {
+            // r = P^{-1} b - P^{-1} (A x)
+            AAO_TRY(matvec_dev(h, x, h->r, nullptr, transpose));
+            AAO_TRY(h->P->apply(h->r, h->w, transpose));
+            launch(k_sub_from, nbl, 256, 0, st, h->w, (const double*)h->bt, nst);
+            AAO_TRY(norm_dev(h, h->w, h->beta));
+            AAO_TRY(read_small(h, sd));
+            beta = h->hsmall->beta;
+            if (!std::isfinite(beta)) {
+                set_error("residual became non-finite");
+                status = AAO_ERR_NONFINITE;
+                break;
+            }
+            if (beta0 < 0.0) {
+                beta0 = beta;
+                // k_givens tests |g_{k+1}| <= tol * beta[1]: the reference is beta_0 here
+                AAO_CUDA_TRY(cudaMemcpyAsync(h->beta + 1, h->beta, sizeof(double), cudaMemcpyDeviceToDevice, st));
+            }
+            if (beta <= tol * beta0) {
+                loc.converged = 1;
+                break;
+            }
+            if (total >= h->opt.maxit) break;
+            Vec<double> V0{h->V, nullptr, nst};
+            launch(k_scale_store<double, double>, nbp, ntp, 0, st, pmo, (int)rows, 1, (const int*)nullptr,
+                   (const double*)h->w, nst, (const double*)h->beta, 0LL, V0);
+            launch(k_outer_init, 1, 32, 0, st, h->gv, m, h->beta, h->flags);
+            AAO_LAUNCH_CHECK();
+            bool stop = false;
+            for (int k = 0; k < m; ++k) {
+                NvtxRange iter_("aao.outer_iteration");
+                ++total;
+                double* Vk = h->V + (long long)k * nst;
+                AAO_TRY(matvec_dev(h, Vk, h->r, nullptr, transpose));
+                AAO_TRY(h->P->apply(h->r, h->w, transpose));
+                {
+                    NvtxRange ortho_("aao.orthogonalize");
+                    Vec<double> none{};
+                    Vec<double> Vfirst{h->V, nullptr, nst};
+                    launch(k_mgs<double, double>, rgrid, kBlock, 0, st, n0, rows, 1, nullptr, h->w, nst, none,
+                           nullptr, Vfirst, 0, red, h->H + k);
+                    for (int i = 1; i <= k + 1; ++i) {
+                        Vec<double> Vp{h->V + (long long)(i - 1) * nst, nullptr, nst};
+                        Vec<double> Vn = i <= k ? Vec<double>{h->V + (long long)i * nst, nullptr, nst} : none;
+                        launch(k_mgs<double, double>, rgrid, kBlock, 0, st, n0, rows, 1, nullptr, h->w, nst, Vp,
+                               h->H + (i - 1) * m + k, Vn, 0, red, h->H + i * m + k);
+                    }
+                }
+                launch(k_givens, 1, 32, 0, st, 1, k, m, h->H, 0, h->cs, h->sn, h->gv, h->beta + 1, tol, h->flags,
+                       h->flags + 1, h->flags + 2, h->resid);
+                AAO_LAUNCH_CHECK();
+                AAO_TRY(read_small(h, sd));
+                h->P->accumulate_times();
+                if (loc.n_history < 128) loc.history[loc.n_history++] = h->hsmall->resid / beta0;
+                if (h->hsmall->nonfinite || h->P->nonfinite_flag()) {
+                    set_error("non-finite Krylov coefficient");
+                    status = AAO_ERR_NONFINITE;
+                    stop = true;
+                    break;
+                }
+                if (!h->hsmall->active || total >= h->opt.maxit) break;
+                Vec<double> Vn{h->V + (long long)(k + 1) * nst, nullptr, nst};
+                launch(k_scale_store<double, double>, nbp, ntp, 0, st, pmo, (int)rows, 1, (const int*)nullptr,
+                       (const double*)h->w, nst, h->H + (k + 1) * m + k, 0, Vn);
+                AAO_LAUNCH_CHECK();
+            }
+            if (stop) break;
+            launch(k_hess_solve, 1, 32, 0, st, 1, m, h->H, 0, h->gv, h->flags + 1, h->y, h->flags + 3);
+            Vec<double> Vc{h->V, nullptr, nst};
+            launch(k_combine<double, double>, nbp, ntp, 0, st, pmo, (int)rows, 1, Vc, nst, (const double*)h->y, m,
+                   (const int*)(h->flags + 1), x, nst, 1);
+            AAO_LAUNCH_CHECK();
+        }
+        loc.outer_its = total;
+        // true residual of the final iterate
+        AAO_TRY(matvec_dev(h, x, h->r, b, transpose));
+        AAO_TRY(norm_dev(h, h->r, h->beta));
+        AAO_TRY(read_small(h, sd));
+        loc.rel_res = h->hsmall->beta / bnorm;
+        if (status == AAO_OK && !loc.converged) {
+            set_error("FGMRES reached maxit");
+            status = AAO_ERR_NOT_CONVERGED;
+        }
+    }
+    AAO_CUDA_TRY(cudaStreamSynchronize(st));
+    loc.inner_its_total = h->P->inner_its();
+    loc.t_theta_ms = h->P->t_theta_ms;
+    loc.t_schur_ms = h->P->t_schur_ms;
+    loc.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = loc;
+    return status;
+}
+
+// The outer solver the options select.
+static aao_status outer_solve(Handle* h, const double* b, double* x, int x0_given, int transpose, aao_info* info,
+                              SmallDev* sd) {
+    if (h->opt.precond_side == 1) return fgmres_left(h, b, x, x0_given, transpose, info, sd);
+    return fgmres(h, b, x, x0_given, transpose, info, sd);
+}
+
 PrecondBase* make_precond(Handle* h, int prec_P, int prec_Pint) {
     if (prec_P == AAO_FP64) return make_precond_f64(h);
     if (prec_P == AAO_FP32) return make_precond_f32(h, prec_Pint);
@@ -658,6 +812,7 @@ void aao_rk_default_options(aao_options* o) {
     o->ckpt_every = 0;
     o->stream = nullptr;
     o->mgrit_m = 0;
+    o->precond_side = 0;
 }
 
 const char* aao_rk_last_error(void) { return get_error(); }
@@ -774,8 +929,10 @@ aao_status aao_rk_set_options(aao_rk_handle hh, const aao_options* o) {
     const aao_options& c = hh->h.opt;
     if (o->prec_P != c.prec_P || o->prec_Pint != c.prec_Pint || o->mg_cycles != c.mg_cycles ||
         o->mg_pre != c.mg_pre || o->mg_post != c.mg_post || o->restart > c.restart || o->restart < 1 ||
-        (o->inner_maxit != 0 && o->inner_maxit != c.inner_maxit) || o->mgrit_m != c.mgrit_m) {
-        set_error("precisions, multigrid shape, inner_maxit, mgrit_m and a larger restart are fixed at set-up");
+        (o->inner_maxit != 0 && o->inner_maxit != c.inner_maxit) || o->mgrit_m != c.mgrit_m ||
+        o->precond_side != c.precond_side) {
+        set_error("precisions, multigrid shape, inner_maxit, mgrit_m, precond_side and a larger restart are "
+                  "fixed at set-up");
         return AAO_ERR_ARG;
     }
     aao_options n = *o;
@@ -863,7 +1020,7 @@ aao_status aao_rk_solve_rhs(aao_rk_handle hh, const double* rhs, double* x, int 
     if (x0_given && xd != x) {
         AAO_CUDA_TRY(cudaMemcpyAsync(xd, x, sizeof(double) * h->nst, cudaMemcpyHostToDevice, h->stream));
     }
-    aao_status s = fgmres(h, bd, xd, x0_given, 0, info, hh->sd);
+    aao_status s = outer_solve(h, bd, xd, x0_given, 0, info, hh->sd);
     aao_status s2 = stage_out_end(hh, x, xd, (size_t)h->nst);
     return s != AAO_OK ? s : s2;
 }
@@ -886,7 +1043,7 @@ aao_status aao_rk_solve(aao_rk_handle hh, const double* f, int f_time_dep, const
     if (x0_given && xd != x) {
         AAO_CUDA_TRY(cudaMemcpyAsync(xd, x, sizeof(double) * h->nst, cudaMemcpyHostToDevice, h->stream));
     }
-    aao_status s = fgmres(h, h->rhs, xd, x0_given, 0, info, hh->sd);
+    aao_status s = outer_solve(h, h->rhs, xd, x0_given, 0, info, hh->sd);
     aao_status s2 = stage_out_end(hh, x, xd, (size_t)h->nst);
     return s != AAO_OK ? s : s2;
 }
@@ -907,7 +1064,7 @@ aao_status aao_rk_adjoint_solve(aao_rk_handle hh, const double* dJdx, double* la
     AAO_TRY(stage_in(hh, dJdx, (size_t)h->nst, hh->stage_in, &bd));
     double* ld;
     AAO_TRY(stage_out_begin(lambda, hh->stage_out, &ld));
-    aao_status s = fgmres(h, bd, ld, 0, 1, info, hh->sd);
+    aao_status s = outer_solve(h, bd, ld, 0, 1, info, hh->sd);
     if (s != AAO_OK && s != AAO_ERR_NOT_CONVERGED) return s;
     if (grad_kappa && h->q1) {
         set_error("grad_kappa is defined for the finite-difference discretisation only");

@@ -47,8 +47,9 @@ def test_struct_layouts_match_header_sizes():
     assert ctypes.sizeof(_lib.aao_tableau) == 4 + 4 + 8 * 64 + 8 * 8 + 8 * 8
     assert ctypes.sizeof(_lib.aao_info) == 4 + 4 + 8 + 8 + 4 + 4 + 8 * 3 + 4 + 4 + 8 * 128
     # tol, restart, maxit, inner_maxit, (pad), inner_tol, mg_cycles, mg_pre, mg_post, (pad), mg_omega,
-    # cheb_steps, prec_P, prec_Pint, ckpt_every, stream, mgrit_m, (pad)
+    # cheb_steps, prec_P, prec_Pint, ckpt_every, stream, mgrit_m, precond_side
     assert ctypes.sizeof(_lib.aao_options) == 8 + 4 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 4 + 8 + 4 * 4 + 8 + 4 + 4
+    assert _lib.aao_options.precond_side.offset == 84
     assert _lib.aao_options.mgrit_m.offset == 80
 
 
@@ -114,6 +115,7 @@ SETUP_BAD = [
     ("opts.prec_P", 7, b"precision"), ("fp64_fp32", None, b"FP64"), ("bf16_fp32", None, b"16-bit"),
     ("fp16_bf16", None, b"16-bit"), ("null_grid", None, b"null"), ("null_out", None, b"null output"),
     ("opts.mgrit_m", 1, b"mgrit_m"), ("opts.mgrit_m", 3, b"mgrit_m"), ("opts.mgrit_m", -2, b"mgrit_m"),
+    ("opts.precond_side", 2, b"precond_side"),
 ]
 
 

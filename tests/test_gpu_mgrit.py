@@ -28,8 +28,11 @@ def make(ns, nt, m, method="radau", s=2, prec="fp64", disc="fd", **kw):
     return S, op, P
 
 
+# 2D grids with a cluster plan take the lock-step schedule (batched relaxation steps); 3D grids and
+# 100 x 12 (no cluster plan) take the dataflow schedule over worker streams
 CASES = [((24, 20), 8, 4, "radau", 3, "fd"), ((40, 36), 16, 8, "radau", 2, "fd"), ((33, 17), 6, 2, "gauss", 2, "fd"),
-         ((7, 6, 5), 6, 3, "radau", 2, "fd"), ((10, 12), 4, 2, "radau", 2, "q1"), ((48, 40), 4, 4, "radau", 3, "fd")]
+         ((7, 6, 5), 6, 3, "radau", 2, "fd"), ((10, 12), 4, 2, "radau", 2, "q1"), ((48, 40), 4, 4, "radau", 3, "fd"),
+         ((100, 12), 8, 4, "radau", 2, "fd"), ((9, 8, 10), 12, 3, "gauss", 2, "fd")]
 
 
 @pytest.mark.parametrize("ns,nt,m,method,s,disc", CASES)
