@@ -62,14 +62,16 @@ def parse():
                    help="extra configurations (the default is the benchmark line)")
     p.add_argument("--precond-case", action="store_true",
                    help="small case for profiler captures: --steps applications of P_tilde (FP32) on the "
-                        "256x256 Radau IIA s=3 grid with 16 time steps; prints ms per application")
+                        "256x256 Radau IIA s=3 grid with 16 time steps (MGRIT with --mgrit-m); prints ms per "
+                        "application")
     p.add_argument("--theta-case", action="store_true",
                    help="profiler case: --steps batched Theta_tilde solves over all 128 time blocks of the "
                         "benchmark grid (256x256, s=3, P_tilde FP32; vectors of 100 MB, larger than L2)")
     p.add_argument("--matvec-case", action="store_true",
                    help="profiler case: --steps FP64 all-at-once matvecs at the benchmark size (269 MB vectors)")
-    p.add_argument("--mgrit-m", type=int, default=8,
-                   help="MGRIT coarsening factor for S_tilde's recurrence (0: forward substitution)")
+    p.add_argument("--mgrit-m", type=int, default=-1,
+                   help="MGRIT coarsening factor for S_tilde's recurrence (0: forward substitution; -1: the "
+                        "autotuner times one P_tilde application per candidate and takes the fastest)")
     p.add_argument("--cpu-sample", default=None, choices=["c1", "reduced", "c2"],
                    help=argparse.SUPPRESS)   # one oracle timing, run in a child with a fixed thread count
     return p.parse_args()
@@ -96,8 +98,10 @@ def batched_arm(args):
     solvers, fs, us, xs = [], [], [], []
     for w in ws:
         st = torch.cuda.Stream(device=dev)
+        m_req = 8 if args.mgrit_m < 0 else args.mgrit_m
+        m = m_req if m_req > 1 and w.nt % m_req == 0 and w.nt > m_req else 0
         solvers.append(Solver(w.n, w.T, w.nt, tableau=radau_iia(w.s), prec_P=args.prec, inner_maxit=3,
-                              inner_tol=1e-3, tol=w.tol, stream=st.cuda_stream))
+                              inner_tol=1e-3, tol=w.tol, stream=st.cuda_stream, mgrit_m=m))
         fs.append(torch.from_numpy(w.f).to(dev))
         us.append(torch.from_numpy(w.u0).to(dev))
         xs.append(torch.zeros(solvers[-1].n_st, dtype=torch.float64, device=dev))
@@ -118,7 +122,10 @@ def batched_arm(args):
     line = {"metric": "batched uneven solves to 1e-8: wall time of the batch", "value": t, "unit": "s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": f"f64/{args.prec}",
-            "data": "synthetic", "config": {"workload": "batched64", "problems": len(ws), "n_st_total": nst},
+            "data": "synthetic", "config": {"workload": "batched64", "problems": len(ws), "n_st_total": nst,
+                                            "schur": f"MGRIT m = {8 if args.mgrit_m < 0 else args.mgrit_m} "
+                                                     f"where it divides nt",
+                                            "execution": "one host thread and stream per problem"},
             "dofs_its_per_s": sum(S.n_st * i for S, i in zip(solvers, its)) / t,
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "outer_its_min_max": [min(its), max(its)], "all_converged": all(i.converged for i in infos)}
@@ -137,7 +144,8 @@ def adjoint_arm(args):
     from paper_2609_16863_gb300.autograd import heat_solve
     dev = torch.device("cuda", 0)
     w = synth.workload_adjoint_2d()
-    mg_m = args.mgrit_m if w.nt % max(args.mgrit_m, 1) == 0 else 0
+    m_req = 8 if args.mgrit_m < 0 else args.mgrit_m
+    mg_m = m_req if w.nt % max(m_req, 1) == 0 else 0
     cfg = dict(n=w.n, T=w.T, nt=w.nt, tableau=radau_iia(w.s), prec_P=args.prec, tol=1e-9, maxit=200, ckpt_every=8,
                inner_maxit=3, inner_tol=1e-3, mgrit_m=mg_m)
     lo = w.nt * w.nx
@@ -379,7 +387,9 @@ def precond_case(args):
     import synth
     from paper_2609_16863_gb300 import Solver, radau_iia
     w = synth.workload_fp32_precond_2d(N=256, nt=16, s=3)
-    S = Solver(w.n, w.T, w.nt, tableau=radau_iia(3), prec_P=args.prec, inner_maxit=3, inner_tol=1e-3)
+    m_req = 8 if args.mgrit_m < 0 else args.mgrit_m
+    m = m_req if w.nt % max(m_req, 1) == 0 and w.nt > m_req else 0
+    S = Solver(w.n, w.T, w.nt, tableau=radau_iia(3), prec_P=args.prec, inner_maxit=3, inner_tol=1e-3, mgrit_m=m)
     g = torch.Generator(device="cuda:0").manual_seed(5)
     r = torch.randn(S.n_st, dtype=torch.float64, device="cuda:0", generator=g)
     z = torch.zeros_like(r)
@@ -392,7 +402,7 @@ def precond_case(args):
         S.precond_apply(r, z)
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"case": "precond_apply fd2d_n256_radau3_nt16", "prec": args.prec,
+    print(json.dumps({"case": "precond_apply fd2d_n256_radau3_nt16", "prec": args.prec, "mgrit_m": m,
                       "ms_per_apply": e0.elapsed_time(e1) / max(args.steps, 1)}))
     S.close()
 
@@ -502,9 +512,16 @@ def main():
             dist.barrier()
 
     w = workload(args.small, args.workload)
-    mg_m = args.mgrit_m if w.nt % max(args.mgrit_m, 1) == 0 else 0
     from paper_2609_16863_gb300.tableau import make as make_tableau
     common = dict(tableau=make_tableau(w.method, w.s), tol=w.tol, restart=20, maxit=100, stream=stream.cuda_stream)
+    tuned = None
+    if args.mgrit_m < 0:
+        from paper_2609_16863_gb300.tune import tune_mgrit
+        mg_m, tuned = tune_mgrit(w.n, w.T, w.nt, tableau=make_tableau(w.method, w.s), prec_P=args.prec,
+                                 inner_maxit=3, inner_tol=1e-3, restart=1)
+        tuned = {str(k): round(v, 3) for k, v in tuned.items()}
+    else:
+        mg_m = args.mgrit_m if w.nt % max(args.mgrit_m, 1) == 0 else 0
     S = Solver(w.n, w.T, w.nt, prec_P=args.prec, inner_maxit=3, inner_tol=1e-3, mgrit_m=mg_m, **common)
     f = torch.from_numpy(w.f).to(dev)
     u0 = torch.from_numpy(w.u0).to(dev)
@@ -588,7 +605,8 @@ def main():
         for ln in lib.aao_rk_profile_report().decode().splitlines():
             name, n, kms, kby = ln.split("\t")
             short = name
-            for tok in ("k_cluster_mg", "k_vcycle_tail", "k_smooth2", "k_smooth_rows", "k_smooth", "k_resid_restrict",
+            for tok in ("k_strip2dIfLi0", "k_strip2dIfLi1", "k_strip2dIfLi2", "k_strip2dIdLi0", "k_strip2dIdLi1",
+                        "k_strip2dIdLi2", "k_cluster_mg", "k_vcycle_tail", "k_smooth2", "k_smooth_rows", "k_smooth", "k_resid_restrict",
                         "k_residual_rows", "k_residual", "k_restrict", "k_prolong_smooth", "k_prolong_add_rows",
                         "k_prolong_add", "k_coarse_solve", "k_rana_rhs", "k_theta", "k_mgs", "k_norm", "k_scale_store",
                         "k_combine", "k_matvec", "k_givens", "k_hess_solve", "k_schur_update_b", "k_schur_update",
@@ -597,6 +615,9 @@ def main():
                 if tok in name:
                     short = tok
                     break
+            if short.startswith("k_strip2dI"):
+                mode = {"0": "smooth", "1": "smooth_zero", "2": "residual"}[short[-1]]
+                short = f"k_strip2d<{'float' if short[10] == 'f' else 'double'}, {mode}>"
             rows.append({"kernel": short, "mangled": name, "launches": int(n), "ms": float(kms), "bytes": float(kby)})
         rows.sort(key=lambda r: -r["ms"])
         return rows, pms.value
@@ -644,7 +665,14 @@ def main():
     rows_t, tot_t = profiled(lambda: S.inner_solve(w.nt, Rb, Zb))
     roof_theta = roof_of(rows_t[0], tot_t)
     roof_theta["measured"] = "CUDA events around each launch of one batched inner solve over all nt blocks"
-    roof_theta["traffic"] = profile_traffic("theta_phase_fd2d_n256_nt128", f"{args.prec} {rows_t[0]['mangled']}")
+    roof_theta["traffic"] = profile_traffic("theta_phase_fd2d_n256_nt128", f"{args.prec} {rows_t[0]['kernel']}")
+    # the dominant kernel of the phase that streams through HBM (the on-chip V-cycle tail excluded)
+    stream_rows = [r for r in rows_t if "vcycle_tail" not in r["mangled"] and "cluster" not in r["mangled"]]
+    roof_stream = roof_of(stream_rows[0], tot_t) if stream_rows else None
+    if roof_stream:
+        roof_stream["measured"] = roof_theta["measured"]
+        roof_stream["traffic"] = profile_traffic("theta_phase_fd2d_n256_nt128",
+                                                 f"{args.prec} {stream_rows[0]['kernel']}")
     top_theta = [{"kernel": r["kernel"], "launches": r["launches"], "ms": round(r["ms"], 3),
                   "algorithmic_GB/s": round(r["bytes"] / (r["ms"] * 1e-3) / 1e9, 1) if r["ms"] > 0 else 0.0,
                   "frac": round(r["bytes"] / (r["ms"] * 1e-3) / 1e9 / peak, 3) if r["ms"] > 0 else 0.0}
@@ -665,6 +693,7 @@ def main():
                            "precond": f"P_tilde {args.prec}, inner GMRES 3/1e-3, 3 V(2,2)-cycles",
                            "schur": (f"two-level MGRIT, m = {mg_m}, F-relaxation, one iteration" if mg_m
                                      else "forward substitution"),
+                           "schur_autotune_ms_per_precond_apply": tuned,
                            "outer": "FP64 FGMRES(20), tol 1e-8",
                            "l2": "working set larger than L2 (no flush)", "parallelism": "replicas",
                            "small_check_only": bool(args.small)},
@@ -675,7 +704,8 @@ def main():
                 "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * (2 * S.nx),
                         "d2h_bytes_per_step": 8 * S.n_st},
                 "gpu_launches": launches // max(1, args.steps) * args.steps,
-                "roofline": roof, "roofline_theta_phase": roof_theta, "kernels_top": top,
+                "roofline": roof, "roofline_theta_phase": roof_theta, "roofline_theta_streaming": roof_stream,
+                "kernels_top": top,
                 "kernels_theta_phase": top_theta, "cpu_baseline": cpu, "clocks": ck}
         print(json.dumps(line), flush=True)
     S.close()

@@ -7,5 +7,6 @@ block-triangular preconditioner (hand-written CUDA for sm_103a behind a C ABI).
 """
 from .tableau import gauss_legendre, radau_iia
 from .api import Info, Solver, solve_batched
+from .tune import tune_mgrit
 
-__all__ = ["Solver", "Info", "solve_batched", "radau_iia", "gauss_legendre"]
+__all__ = ["Solver", "Info", "solve_batched", "radau_iia", "gauss_legendre", "tune_mgrit"]

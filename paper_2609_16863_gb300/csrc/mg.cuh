@@ -363,10 +363,11 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_smooth_rows(LevelOp<S> op, Pt
 // a thread owns V consecutive columns (one 16-byte vector) of a strip of RS rows and keeps the
 // rows j-1, j, j+1 of x in registers while it walks down the strip, so each point costs one
 // vector load of x, one of b and one store (plus two scalar halo loads per row and two halo
-// rows per strip).  MODE 0: damped Jacobi x + omega (b - A x) / a_PP; MODE 1: the same from
-// x = 0 (omega b / a_PP, x is not read); MODE 2: the residual b - A x.  Same arithmetic as
-// level_apply_k<4>.  Block: 256 threads = (n0 / V) threads per row x strips; grid
-// (ceil(n1 / (strips RS)), items).
+// rows per strip); the next row's loads are issued before the current row is computed.
+// MODE 0: damped Jacobi x + (omega / a_PP) (b - A x); MODE 1: the same from x = 0
+// ((omega / a_PP) b, x is not read); MODE 2: the residual b - A x.  A x as level_apply_k<4>;
+// the Jacobi weight omega / a_PP as the cluster V-cycle.  Block: 256 threads = (n0 / V)
+// threads per row x strips; grid (ceil(n1 / (strips RS)), items).
 // ---------------------------------------------------------------------------
 template <class S> struct Vec16;
 template <> struct Vec16<float> {
@@ -404,8 +405,7 @@ __global__ void __launch_bounds__(kStripThreads) k_strip2d(LevelOp<S> op, int B,
     S* O = out.d + (long long)b * out.bs;
     const S hx2 = S(g.hx2), hy2 = S(g.hy2);
     const S kd = S(2) * hx2 + S(2) * hy2;
-    const S dg = op.sigma + op.c * kd;
-    S sr[V], pr[V], nr[V];
+    const S wgt = omega / (op.sigma + op.c * kd);      // omega / a_PP, as the cluster V-cycle
     auto load_row = [&](int j, S* dst) {
         if (j >= 0 && j < n1) {
             VT v = *reinterpret_cast<const VT*>(X + (long long)j * n0 + c0);
@@ -417,32 +417,44 @@ __global__ void __launch_bounds__(kStripThreads) k_strip2d(LevelOp<S> op, int B,
             for (int t = 0; t < V; ++t) dst[t] = S(0);
         }
     };
+    auto load_b = [&](int j, S* dst) {
+        VT v = *reinterpret_cast<const VT*>(Bp + (long long)j * n0 + c0);
+        const S* q = reinterpret_cast<const S*>(&v);
+#pragma unroll
+        for (int t = 0; t < V; ++t) dst[t] = q[t];
+    };
+    // the loads of row j + 1 are issued before row j is computed (two rows in flight per thread)
+    S sr[V], pr[V], nr[V], bq[V], nn[V], bn[V];
+    S w = S(0), e = S(0), wn = S(0), en = S(0);
+    load_b(j0, bq);
     if (MODE != 1) {
         load_row(j0 - 1, sr);
         load_row(j0, pr);
+        load_row(j0 + 1, nr);
+        w = c0 > 0 ? X[(long long)j0 * n0 + c0 - 1] : S(0);
+        e = c0 + V < n0 ? X[(long long)j0 * n0 + c0 + V] : S(0);
     }
     for (int j = j0; j < j1; ++j) {
-        const VT bvec = *reinterpret_cast<const VT*>(Bp + (long long)j * n0 + c0);
-        const S* bq = reinterpret_cast<const S*>(&bvec);
+        const bool more = j + 1 < j1;
+        if (more) {
+            load_b(j + 1, bn);
+            if (MODE != 1) {
+                load_row(j + 2, nn);
+                wn = c0 > 0 ? X[(long long)(j + 1) * n0 + c0 - 1] : S(0);
+                en = c0 + V < n0 ? X[(long long)(j + 1) * n0 + c0 + V] : S(0);
+            }
+        }
         S res[V];
         if (MODE == 1) {
 #pragma unroll
-            for (int t = 0; t < V; ++t) res[t] = omega * bq[t] / dg;
+            for (int t = 0; t < V; ++t) res[t] = wgt * bq[t];
         } else {
-            load_row(j + 1, nr);
-            const S w = c0 > 0 ? X[(long long)j * n0 + c0 - 1] : S(0);
-            const S e = c0 + V < n0 ? X[(long long)j * n0 + c0 + V] : S(0);
 #pragma unroll
             for (int t = 0; t < V; ++t) {
                 const S uP = pr[t], uW = t == 0 ? w : pr[t - 1], uE = t == V - 1 ? e : pr[t + 1];
                 const S K = hx2 * (S(2) * uP - uW - uE) + hy2 * (S(2) * uP - sr[t] - nr[t]);
                 const S Au = op.sigma * uP + op.c * K;
-                res[t] = MODE == 0 ? uP + omega * (bq[t] - Au) / dg : bq[t] - Au;
-            }
-#pragma unroll
-            for (int t = 0; t < V; ++t) {
-                sr[t] = pr[t];
-                pr[t] = nr[t];
+                res[t] = MODE == 0 ? uP + wgt * (bq[t] - Au) : bq[t] - Au;
             }
         }
         VT ov;
@@ -450,6 +462,19 @@ __global__ void __launch_bounds__(kStripThreads) k_strip2d(LevelOp<S> op, int B,
 #pragma unroll
         for (int t = 0; t < V; ++t) oq[t] = res[t];
         *reinterpret_cast<VT*>(O + (long long)j * n0 + c0) = ov;
+        if (more) {
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                bq[t] = bn[t];
+                if (MODE != 1) {
+                    sr[t] = pr[t];
+                    pr[t] = nr[t];
+                    nr[t] = nn[t];
+                }
+            }
+            w = wn;
+            e = en;
+        }
     }
 }
 
@@ -471,6 +496,128 @@ inline dim3 strip_grid(const LevelOp<S>& op, int B) {
     const int tpr = op.g.n0 / Vec16<S>::n;
     const int rows_per_block = (kStripThreads / tpr) * kStripRows;
     return dim3((unsigned)((op.g.n1 + rows_per_block - 1) / rows_per_block), (unsigned)B, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Finest matrix-free level (sigma I + c K, kappa = 1, 2D or 3D) in 16-bit storage with per-row
+// scales: a thread owns 8 consecutive columns of a row (one 16-byte vector), the threads of a row
+// form a group of gs lanes within one warp (gs = the power of two >= n0 / 8), so the row's scale
+// is a shuffle reduction over the group and no block barrier is needed.  MODE 0: damped Jacobi
+// x + omega (b - A x) / a_PP; MODE 1: from x = 0; MODE 2: residual b - A x.  Same arithmetic as
+// level_apply_k and the same scale rule as pt_store.  Block 256 threads (256 / gs rows); grid
+// (ceil(R / rows per block), items).
+// ---------------------------------------------------------------------------
+constexpr int kVecThreads = 256;
+
+template <class S>
+__device__ __forceinline__ void vec8_load(const S* p, float sc, float* out) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    const S* q = reinterpret_cast<const S*>(&v);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) out[t] = PT<S>::ld(q[t]) * sc;
+}
+
+template <class S, int MODE>
+__global__ void __launch_bounds__(kVecThreads) k_vec16(LevelOp<S> op, int gs, int B, const int* active, Vec<S> xin,
+                                                       Vec<S> bv, Vec<S> out, float omega) {
+    pdl_prologue();
+    static_assert(PT<S>::scaled, "16-bit storage only");
+    const Geo g = op.g;
+    const int b = blockIdx.y;
+    if (b >= B || (active && !active[b])) return;
+    const int n0 = g.n0, tpr = n0 / 8;
+    const int lane = threadIdx.x & 31, grp = lane / gs, gl = lane - grp * gs;
+    const int rows_per_warp = 32 / gs;
+    const long long row = ((long long)blockIdx.x * (kVecThreads / 32) + (threadIdx.x >> 5)) * rows_per_warp + grp;
+    const bool valid = row < g.R && gl < tpr;       // every lane of a row's group takes part in its reduction
+    int j = 0, k = 0;
+    if (row < g.R) row_jk(g, row, j, k);
+    const int c0 = gl * 8;
+    const long long base = (long long)b * bv.bs;    // the same item stride for x, b and out
+    const S* X = MODE == 1 ? nullptr : xin.d + (long long)b * xin.bs;
+    const float* XS = MODE == 1 ? nullptr : xin.sc + (long long)b * xin.bs / n0;
+    const S* Bd = bv.d + base;
+    const float* BS = bv.sc + base / n0;
+    float res[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) res[t] = 0.f;
+    if (valid) {
+        const float hx2 = float(g.hx2), hy2 = float(g.hy2), hz2 = float(g.hz2);
+        float kd = 2.f * hx2 + 2.f * hy2;
+        if (g.d == 3) kd += 2.f * hz2;
+        const float dg = float(op.sigma) + float(op.c) * kd;
+        float bq[8];
+        vec8_load(Bd + row * n0 + c0, BS[row], bq);
+        if (MODE == 1) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) res[t] = omega * bq[t] / dg;
+        } else {
+            float P[8], Sv[8], Nv[8], Dv[8], Uv[8];
+            vec8_load(X + row * n0 + c0, XS[row], P);
+            if (j > 0) vec8_load(X + (row - 1) * n0 + c0, XS[row - 1], Sv);
+            else for (int t = 0; t < 8; ++t) Sv[t] = 0.f;
+            if (j + 1 < g.n1) vec8_load(X + (row + 1) * n0 + c0, XS[row + 1], Nv);
+            else for (int t = 0; t < 8; ++t) Nv[t] = 0.f;
+            if (g.d == 3) {
+                if (k > 0) vec8_load(X + (row - g.n1) * n0 + c0, XS[row - g.n1], Dv);
+                else for (int t = 0; t < 8; ++t) Dv[t] = 0.f;
+                if (k + 1 < g.n2) vec8_load(X + (row + g.n1) * n0 + c0, XS[row + g.n1], Uv);
+                else for (int t = 0; t < 8; ++t) Uv[t] = 0.f;
+            }
+            const float w = c0 > 0 ? PT<S>::ld(X[row * n0 + c0 - 1]) * XS[row] : 0.f;
+            const float e = c0 + 8 < n0 ? PT<S>::ld(X[row * n0 + c0 + 8]) * XS[row] : 0.f;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const float uP = P[t], uW = t == 0 ? w : P[t - 1], uE = t == 7 ? e : P[t + 1];
+                float K = hx2 * (2.f * uP - uW - uE) + hy2 * (2.f * uP - Sv[t] - Nv[t]);
+                if (g.d == 3) K += hz2 * (2.f * uP - Dv[t] - Uv[t]);
+                const float Au = float(op.sigma) * uP + float(op.c) * K;
+                res[t] = MODE == 0 ? uP + omega * (bq[t] - Au) / dg : bq[t] - Au;
+            }
+        }
+    }
+    // the row's power-of-two scale: maximum over the row's group of lanes
+    float m = 0.f;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) m = fmaxf(m, fabsf(res[t]));
+    for (int o = gs >> 1; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int ex = 0;
+    float sc = 1.f, inv = 1.f;
+    if (m > 0.f && m <= 3.0e38f) {
+        frexpf(m, &ex);
+        sc = ldexpf(1.f, ex - 14);
+        inv = ldexpf(1.f, 14 - ex);
+    }
+    if (valid) {
+        uint4 ov;
+        S* oq = reinterpret_cast<S*>(&ov);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) oq[t] = PT<S>::st(res[t] * inv);
+        *reinterpret_cast<uint4*>(out.d + (long long)b * out.bs + row * n0 + c0) = ov;
+        if (gl == 0) out.sc[(long long)b * out.bs / n0 + row] = sc;
+    }
+}
+
+// Whether a level takes k_vec16: the matrix-free finest level with kappa = 1, 16-bit storage,
+// rows of whole 16-byte vectors with at most 32 vectors per row.
+template <class S>
+inline bool vec16_ok(const LevelOp<S>& op) {
+    if constexpr (!PT<S>::scaled) {
+        return false;
+    } else {
+        const int n0 = op.g.n0;
+        return op.fine && op.faces.fx == nullptr && n0 % 8 == 0 && n0 / 8 <= 32;
+    }
+}
+inline int vec16_group(int n0) {
+    int gs = 1;
+    while (gs < n0 / 8) gs <<= 1;
+    return gs;
+}
+template <class S>
+inline dim3 vec16_grid(const LevelOp<S>& op, int B) {
+    const int rows_per_block = (kVecThreads / 32) * (32 / vec16_group(op.g.n0));
+    return dim3((unsigned)((op.g.R + rows_per_block - 1) / rows_per_block), (unsigned)B, 1);
 }
 
 // r = b - A x for unscaled storage, RPT rows per thread (as k_smooth_rows).

@@ -667,6 +667,14 @@ class Precond : public PrecondBase {
     // Large batches of the 2D matrix-free level (kappa = 1) take the streaming strip kernel.
     void launch_smooth(int kind, dim3 grid, dim3 block, const LevelOp<SI>& op, const PtMap& pm, int B, const int* act,
                        Vec<SI> x, Vec<SI> b, Vec<SI> out, A om) {
+        if constexpr (PT<SI>::scaled) {
+            if (vec16_ok(op)) {
+                const int gs = vec16_group(op.g.n0);
+                if (x.d) launch(k_vec16<SI, 0>, vec16_grid(op, B), kVecThreads, 0, st(), op, gs, B, act, x, b, out, om);
+                else launch(k_vec16<SI, 1>, vec16_grid(op, B), kVecThreads, 0, st(), op, gs, B, act, x, b, out, om);
+                return;
+            }
+        }
         if constexpr (!PT<SI>::scaled) {
             if (kind == 4 && grid.y >= 16 && strip_ok(op)) {
                 if (x.d) launch(k_strip2d<SI, 0>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, om);
@@ -693,6 +701,13 @@ class Precond : public PrecondBase {
     }
     void launch_residual(int kind, dim3 grid, dim3 block, const LevelOp<SI>& op, const PtMap& pm, int B,
                          const int* act, Vec<SI> x, Vec<SI> b, Vec<SI> out) {
+        if constexpr (PT<SI>::scaled) {
+            if (vec16_ok(op) && x.d) {
+                launch(k_vec16<SI, 2>, vec16_grid(op, B), kVecThreads, 0, st(), op, vec16_group(op.g.n0), B, act, x,
+                       b, out, A(0));
+                return;
+            }
+        }
         if constexpr (!PT<SI>::scaled) {
             if (kind == 4 && grid.y >= 16 && strip_ok(op) && x.d) {
                 launch(k_strip2d<SI, 2>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, A(0));
@@ -750,7 +765,9 @@ class Precond : public PrecondBase {
         // bandwidth- or FP64-bound batched phase.  Only on 2D levels and on the
         // matrix-free fine level (a 27-point stored stencil makes the neighbour
         // recomputation too costly).
-        const bool fuse = (long long)B * g.nx <= kFuseMaxPoints && (g.d == 2 || op.fine);
+        // (a finest level that streams through k_vec16 is not fused: its separate sweeps are cheaper
+        // than the fused kernels' recomputation)
+        const bool fuse = (long long)B * g.nx <= kFuseMaxPoints && (g.d == 2 || op.fine) && !vec16_ok(op);
         const bool f2 = fuse && nu1 >= 2, fps = fuse && nu2 >= 1;
         const int pre_l = f2 ? nu1 - 1 : nu1;
         const int post_l = fps ? nu2 : nu2 + 1;

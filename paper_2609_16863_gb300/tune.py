@@ -1,0 +1,47 @@
+"""Schedule autotuner: choose how S_tilde's time recurrence runs for one problem.
+
+The recurrence runs as the forward substitution of Eq. (AppSchur) (mgrit_m = 0) or as one
+two-level MGRIT iteration with coarsening factor m (the parallel implementation of Sec. 5).
+Which is faster depends on the problem: MGRIT does about twice the work of the substitution but
+cuts its dependency chain from nt steps to about 2m + nt/m, which pays where a single step is
+latency-bound (2D grids, whose shifted solves run on one thread-block cluster) and not where one
+step already fills the GPU (large 3D grids).  `tune_mgrit` times one application of P_tilde per
+candidate through the C ABI (after one untimed application that captures the step graphs) and
+returns the fastest candidate with every timing.
+"""
+from __future__ import annotations
+
+from typing import Dict, Iterable, Optional, Sequence, Tuple
+
+from .api import Solver
+
+
+def mgrit_candidates(nt: int, factors: Iterable[int] = (4, 8, 16, 32)) -> list:
+    """0 (substitution) and every factor m that divides nt with at least two intervals."""
+    return [0] + [m for m in factors if nt % m == 0 and nt // m >= 2]
+
+
+def tune_mgrit(n: Sequence[int], T: float, nt: int, candidates: Optional[Iterable[int]] = None,
+               device: str = "cuda:0", **solver_kw) -> Tuple[int, Dict[int, float]]:
+    """Return (best mgrit_m, {mgrit_m: ms per P_tilde application}) for the problem (n, T, nt) with
+    the solver options solver_kw (precision, tableau, inner settings...)."""
+    import torch
+    cands = list(candidates) if candidates is not None else mgrit_candidates(nt)
+    times: Dict[int, float] = {}
+    for m in cands:
+        S = Solver(n, T, nt, mgrit_m=m, **solver_kw)
+        g = torch.Generator(device=device).manual_seed(11)
+        r = torch.randn(S.n_st, dtype=torch.float64, device=device, generator=g)
+        z = torch.zeros_like(r)
+        S.precond_apply(r, z)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        S.precond_apply(r, z)
+        e1.record()
+        torch.cuda.synchronize()
+        times[m] = e0.elapsed_time(e1)
+        S.close()
+        del r, z
+    best = min(times, key=times.get)
+    return best, times

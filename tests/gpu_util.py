@@ -31,14 +31,15 @@ def rel_max(a, b):
     return d / s if s > 0 else d
 
 
-def gpu_plan(sizes, B, cluster=False):
+def gpu_plan(sizes, B, cluster=False, fmt="fp32"):
     """The CUDA path's multigrid memory plan for B items of a hierarchy with level sizes `sizes`
     (finest first), restated from its launch rules for the storage emulation of the oracle:
     up to 32 items of a 2D grid with a cluster plan keep all their V-cycles on chip (one
     thread-block cluster per item); otherwise the levels
     from the first one with at most 4096 (B > 1) or 1024 (B = 1) points down run as one on-chip
     V-cycle, and a level above them fuses its steps when B * points <= 2^20 and it is 2D or the
-    matrix-free finest level."""
+    matrix-free finest level, except a 16-bit finest level whose rows are whole 16-byte vectors
+    (n0 a multiple of 8, at most 256), which streams through separate vectorised sweeps."""
     from oracle.lowprec import Plan
     if cluster and B <= 32:
         return Plan(keep_x=True)
@@ -50,7 +51,9 @@ def gpu_plan(sizes, B, cluster=False):
             break
         lc = l
     d = len(sizes[0])
-    fuse = [B * pts[l] <= (1 << 20) and (d == 2 or l == 0) for l in range(len(sizes))]
+    n0 = sizes[0][0]
+    vec0 = fmt in ("bf16", "fp16") and n0 % 8 == 0 and n0 // 8 <= 32
+    fuse = [B * pts[l] <= (1 << 20) and (d == 2 or l == 0) and not (l == 0 and vec0) for l in range(len(sizes))]
     return Plan(onchip_from=lc, fuse=fuse)
 
 

@@ -48,7 +48,8 @@ def make(ns, nt, s, precP, precI=None, method="radau", inner_tol=0.0):
 
 def emulation(P, precP, precI, B, cluster):
     sizes = P.mg[0].sizes
-    return lp.StoredPreconditioner(P, precP, precI, gpu_plan(sizes, B, cluster), gpu_plan(sizes, 1, cluster))
+    return lp.StoredPreconditioner(P, precP, precI, gpu_plan(sizes, B, cluster, precI),
+                                   gpu_plan(sizes, 1, cluster, precI))
 
 
 def check_step(what, got, ref, n0, fmt, max_ulps):
@@ -68,7 +69,7 @@ def check_step(what, got, ref, n0, fmt, max_ulps):
 # (grid, fmt, a single 2D item runs on a thread-block cluster, allowed units in the last place)
 SHIFTED = [((48, 40), "bf16", True, 1), ((48, 40), "fp16", True, 1), ((48, 40), "fp32", True, 0),
            ((97, 33), "bf16", True, 1), ((64, 64), "fp16", True, 1), ((20, 18, 22), "bf16", False, 16),
-           ((16, 16, 16), "fp16", False, 16), ((130, 70), "fp32", True, 0)]
+           ((16, 16, 16), "fp16", False, 16), ((130, 70), "fp32", True, 0), ((24, 16, 20), "bf16", False, 16)]
 
 
 @pytest.mark.parametrize("ns,fmt,cluster,ulps", SHIFTED)
@@ -124,7 +125,9 @@ INNER_BOUND = {"fp32": 2e-5, "fp16": 1e-3, "bf16": 2e-3}
                                                        ((20, 18, 22), 3, "bf16", "bf16", False),
                                                        ((64, 64), 3, "fp32", "bf16", True),
                                                        ((40, 36), 5, "fp32", "fp32", True),
-                                                       ((48, 40), 40, "bf16", "bf16", False)])
+                                                       ((48, 40), 40, "bf16", "bf16", False),
+                                                       ((64, 32), 36, "fp16", "fp16", False),
+                                                       ((16, 16, 24), 4, "bf16", "bf16", False)])
 def test_inner_solve_matches_storage_emulation(ns, nb, precP, precI, cluster):
     """Batched inner GMRES (3 fixed iterations) per time block; batches of more than 32 items take
     the level kernels and the on-chip tail instead of one cluster per item."""

@@ -85,3 +85,11 @@ def test_mgrit_mixed_solve_against_exact_solution(prec):
     err = np.linalg.norm(host(x) - exact) / np.linalg.norm(exact)
     print(f"MGRIT {prec}: outer its {info.outer_its}, error vs the exact solution {err:.2e}")
     assert info.converged and err <= 1e-8
+
+
+def test_schedule_autotuner_returns_a_timed_candidate():
+    from paper_2609_16863_gb300 import tune_mgrit, radau_iia
+    dev()
+    best, times = tune_mgrit((48, 40), 1.0, 16, tableau=radau_iia(2), prec_P="fp32", inner_maxit=3, inner_tol=1e-3)
+    assert set(times) == {0, 4, 8} and best in times and all(t > 0 for t in times.values())
+    assert times[best] == min(times.values())
