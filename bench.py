@@ -28,6 +28,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -615,6 +616,10 @@ def main():
                 if tok in name:
                     short = tok
                     break
+            mv = re.search(r"k_vec16I(\w+?)Li(\d)E", name)
+            if mv:
+                short = (f"k_vec16<{'bf16' if 'bfloat' in mv.group(1) else 'fp16'}, "
+                         f"{ {'0': 'smooth', '1': 'smooth_zero', '2': 'residual'}[mv.group(2)] }>")
             if short.startswith("k_strip2dI"):
                 mode = {"0": "smooth", "1": "smooth_zero", "2": "residual"}[short[-1]]
                 short = f"k_strip2d<{'float' if short[10] == 'f' else 'double'}, {mode}>"
