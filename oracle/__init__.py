@@ -31,6 +31,11 @@ It is a plain, slow, obviously-correct restatement of the method:
 * ``adjoint``    -- the adjoint solve and gradients of the tracking functional.
 * ``spectral``   -- the exact all-at-once solution for constant-coefficient finite
                     differences, mode by mode in the sine basis (any size).
+* ``relaxed``    -- FGMRES with an iteration-dependent (relaxed) product precision:
+                    an inexact product accepted while its error bound stays below
+                    the inexact-Krylov allowance, which grows as the residual falls
+                    (the paper's future-work direction), and the FP32 product with
+                    its rigorous rounding bound.
 * ``lowprec``    -- P_tilde with its stored vectors rounded to FP32, BF16 or FP16
                     (per-row power-of-two scales) and FP32 arithmetic, the storage
                     emulation of Sec. 4--5 (the paper simulates it with chop).
