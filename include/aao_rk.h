@@ -116,6 +116,15 @@ typedef struct {
                           * P_L = P_tilde and P_R = I (Algorithm 1; the parallel runs of Sec. 5.2),
                           * converged when ||P^{-1} b - P^{-1} A x|| <= tol ||P^{-1} b||, with
                           * rel_res still the true ||b - A x|| / ||b|| */
+    double relax_matvec; /* ell >= 0: iteration-dependent precision of the outer product A z_k (the
+                          * future-work direction of the paper's introduction, after the inexact-Krylov
+                          * bound of Simoncini and Szyld).  0 = every product in FP64.  ell > 0:
+                          * iteration k of a cycle first forms A z_k in FP32 with the a-posteriori bound
+                          * gamma_32 || |A| |z_k| || on its error, and keeps it when the bound is at most
+                          * ell tol ||b|| / (restart |g_k|), |g_k| the current least-squares residual;
+                          * else it recomputes A z_k in FP64.  The stopping test stays on the true FP64
+                          * residual.  Finite differences with right preconditioning only (else
+                          * AAO_ERR_UNSUPPORTED); may be changed by aao_rk_set_options */
 } aao_options;
 
 typedef struct {
@@ -128,6 +137,7 @@ typedef struct {
     double t_total_ms;         /* wall time of the call */
     int n_history;
     double history[128];       /* FGMRES least-squares residual / ||b|| per iteration */
+    int relaxed_matvecs;       /* outer iterations whose product A z_k was kept in FP32 (relax_matvec) */
 } aao_info;
 
 void aao_rk_default_options(aao_options* opts);
@@ -173,6 +183,13 @@ aao_status aao_rk_rhs(aao_rk_handle h, const double* f, int f_time_dep, const do
 
 /* y = A x and y = A^T x in FP64 (Eq. system_all_at_once_RK), n_st each. */
 aao_status aao_rk_matvec(aao_rk_handle h, const double* x, double* y);
+/* The FP32 product of the relaxed outer iteration (aao_options.relax_matvec; the paper's
+ * future-work direction of an iteration-dependent matvec precision): y = fl32(A x) (transpose:
+ * A^T x) with x and every coefficient rounded to FP32 and FP32 arithmetic, and absy = the same
+ * expression over absolute coefficients and inputs, so that |y - A x| <= gamma_32 absy entry by
+ * entry (gamma_d = d u / (1 - d u), u = 2^-24).  Finite differences only (else
+ * AAO_ERR_UNSUPPORTED); x, y, absy are DEVICE arrays of n_st values (else AAO_ERR_ARG). */
+aao_status aao_rk_matvec_relaxed(aao_rk_handle h, const double* x, double* y, double* absy, int transpose);
 aao_status aao_rk_matvec_transpose(aao_rk_handle h, const double* x, double* y);
 
 /* z = P_tilde^{-1} r (Eq. AppPrec, AppSchur) in the handle's precisions;

@@ -34,13 +34,15 @@ class aao_options(C.Structure):
                 ("mg_cycles", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
                 ("mg_omega", C.c_double), ("cheb_steps", C.c_int),
                 ("prec_P", C.c_int), ("prec_Pint", C.c_int), ("ckpt_every", C.c_int),
-                ("stream", C.c_void_p), ("mgrit_m", C.c_int), ("precond_side", C.c_int)]
+                ("stream", C.c_void_p), ("mgrit_m", C.c_int), ("precond_side", C.c_int),
+                ("relax_matvec", C.c_double)]
 
 
 class aao_info(C.Structure):
     _fields_ = [("outer_its", C.c_int), ("inner_its_total", C.c_longlong), ("rel_res", C.c_double),
                 ("converged", C.c_int), ("t_theta_ms", C.c_double), ("t_schur_ms", C.c_double),
-                ("t_total_ms", C.c_double), ("n_history", C.c_int), ("history", C.c_double * 128)]
+                ("t_total_ms", C.c_double), ("n_history", C.c_int), ("history", C.c_double * 128),
+                ("relaxed_matvecs", C.c_int)]
 
 
 H = C.c_void_p
@@ -62,6 +64,7 @@ SIGNATURES = [
     ("aao_rk_rhs", C.c_int, [H, P, C.c_int, P, P]),
     ("aao_rk_matvec", C.c_int, [H, P, P]),
     ("aao_rk_matvec_transpose", C.c_int, [H, P, P]),
+    ("aao_rk_matvec_relaxed", C.c_int, [H, P, P, P, C.c_int]),
     ("aao_rk_precond_apply", C.c_int, [H, P, P]),
     ("aao_rk_precond_apply_transpose", C.c_int, [H, P, P]),
     ("aao_rk_solve", C.c_int, [H, P, C.c_int, P, P, C.c_int, C.POINTER(aao_info)]),

@@ -49,11 +49,13 @@ class Info:
     t_schur_ms: float
     t_total_ms: float
     history: list = field(default_factory=list)
+    relaxed_matvecs: int = 0
 
     @staticmethod
     def from_c(ci: _lib.aao_info) -> "Info":
         return Info(ci.outer_its, ci.inner_its_total, ci.rel_res, bool(ci.converged), ci.t_theta_ms,
-                    ci.t_schur_ms, ci.t_total_ms, [ci.history[i] for i in range(ci.n_history)])
+                    ci.t_schur_ms, ci.t_total_ms, [ci.history[i] for i in range(ci.n_history)],
+                    ci.relaxed_matvecs)
 
 
 class Solver:
@@ -61,14 +63,16 @@ class Solver:
     nt steps, an RK tableau (A, b, c), optional nodal diffusivity kappa.  mgrit_m > 0
     (a divisor of nt) replaces S_tilde's forward substitution by one two-level MGRIT
     iteration with coarsening factor mgrit_m; precond_side="left" runs Algorithm 1 with
-    P_L = P_tilde, P_R = I instead of the right-preconditioned FGMRES."""
+    P_L = P_tilde, P_R = I instead of the right-preconditioned FGMRES.  relax_matvec = ell > 0
+    lets late outer iterations keep an FP32 product A z_k whose error bound is within the
+    inexact-Krylov allowance ell tol ||b|| / (restart |g_k|) (aao_options.relax_matvec)."""
 
     def __init__(self, n: Sequence[int], T: float, nt: int, tableau=None, method: str = "radau", s: int = 2,
                  lens=None, kappa=None, prec_P: str = "fp64", prec_Pint: Optional[str] = None,
                  tol: float = 1e-8, restart: int = 20, maxit: int = 100, inner_maxit: int = 0,
                  inner_tol: float = -1.0, mg_cycles: int = 3, mg_pre: int = 2, mg_post: int = 2,
                  mg_omega: float = 0.8, disc: str = "fd", cheb_steps: int = 20, stream=None, mgrit_m: int = 0,
-                 precond_side: str = "right"):
+                 precond_side: str = "right", relax_matvec: float = 0.0):
         self._lib = _lib.lib()
         self.n = tuple(int(v) for v in n)
         self.dim = len(self.n)
@@ -104,6 +108,7 @@ class Solver:
         o.stream = stream
         o.mgrit_m = mgrit_m
         o.precond_side = {"right": 0, "left": 1}[precond_side]
+        o.relax_matvec = relax_matvec
         self.options = o
         h = C.c_void_p()
         _lib.check(self._lib.aao_rk_setup(C.byref(g), self.tau, self.nt, C.byref(t), C.byref(o), C.byref(h)))
@@ -153,6 +158,13 @@ class Solver:
         fn = self._lib.aao_rk_matvec_transpose if transpose else self._lib.aao_rk_matvec
         _lib.check(fn(self.h, _ptr(x, self.n_st, "x"), _ptr(y, self.n_st, "y")))
         return y
+
+    def matvec_relaxed(self, x, y, absy, transpose=False):
+        """y = fl32(A x) (or A^T x) and absy = its absolute expression, with |y - A x| <= gamma_32
+        absy entry by entry (the relaxed outer product); device arrays of n_st values."""
+        _lib.check(self._lib.aao_rk_matvec_relaxed(self.h, _ptr(x, self.n_st, "x"), _ptr(y, self.n_st, "y"),
+                                                   _ptr(absy, self.n_st, "absy"), int(bool(transpose))))
+        return y, absy
 
     def precond_apply(self, r, z, transpose=False):
         """z = P_tilde^{-1} r (or P_tilde^{-T} r), n_st values each."""

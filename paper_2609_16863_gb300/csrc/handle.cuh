@@ -120,6 +120,8 @@ struct Handle {
     double* Z = nullptr;           // m * nst (right preconditioning)
     double* bt = nullptr;          // nst: P^{-1} b (left preconditioning)
     double* w = nullptr;           // nst
+    double* relax_part = nullptr;  // per-block sums of squares of |A||z| (relaxed FP32 product)
+    int* relax_flag = nullptr;     // [0] keep the FP32 product of this iteration, [1] products kept
     double* r = nullptr;           // nst
     double* rhs = nullptr;         // nst (staging for solve / host inputs)
     double* xs = nullptr;          // nst (staging for host x)

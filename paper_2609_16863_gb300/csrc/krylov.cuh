@@ -827,11 +827,15 @@ static __global__ void __launch_bounds__(kPtMaxThreads) k_apply_M_q1(Geo g, PtMa
 //   y_{v,n}   = l_{v,n} - l_{v,n+1} + sum_i K l_{V,n,i}   (n < nt),  y_{v,nt} = l_{v,nt}
 //   y_{V,n,i} = l_{V,n,i} - tau b_i l_{v,n+1} + tau sum_j a_ji K l_{V,n,j}.
 // rhs != nullptr gives y = rhs - (A x).  Warps with n == nt handle block v_0 / v_nt.
+// skip != nullptr: the launch does nothing when *skip is nonzero (the relaxed outer product kept
+// its FP32 result, k_relax_decide).
 // ---------------------------------------------------------------------------
 
 static __global__ void __launch_bounds__(kBlock) k_matvec(Geo g, int nt, Tab tab, double tau, Faces<double> faces,
-                                                   const double* x, double* y, const double* rhs, int transpose) {
+                                                   const double* x, double* y, const double* rhs, int transpose,
+                                                   const int* skip) {
     pdl_prologue();
+    if (skip && *skip) return;
     long long w = gwarp();
     if (w >= (long long)(nt + 1) * g.R) return;
     int n = (int)(w / g.R);
@@ -882,6 +886,185 @@ static __global__ void __launch_bounds__(kBlock) k_matvec(Geo g, int nt, Tab tab
                 y[yv] = rhs ? rhs[yv] - a : a;
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Relaxed outer product (aao_options.relax_matvec): y = A x (or A^T x) evaluated in FP32 -- x and
+// every coefficient rounded to FP32, every operation in FP32, y stored in FP64 -- beside the
+// absolute expression |A||x| (the same linear expression tree with every coefficient and input
+// replaced by its absolute value, so no cancellation).  Every output is a linear expression tree
+// in the inputs, so fl(y) = sum_t c_t x_t (1 + theta_t) with |theta_t| <= gamma_d, d the number
+// of roundings on the longest path from an input to the output (Higham, Accuracy and Stability of
+// Numerical Algorithms, Lemma 3.1), and |fl(y) - y| <= gamma_d |A||x| entry by entry.  Counted
+// on the stage row with faces in 3D: input 1, difference 1, face product 1, the six-term stencil
+// sum 5, the product with the rounded tau a_ij 1 + 2, the stage sum s + 1: s + 12 <= 20 for
+// s <= 8; kRelaxDepth = 32 over-counts it.  Each block writes the sum of squares of its outputs'
+// absolute expressions to part[blockIdx.x]; absy != nullptr also receives them entry by entry.
+// ---------------------------------------------------------------------------
+constexpr int kRelaxDepth = 32;
+
+struct K32 {
+    float v, a;    // (K u)_P in FP32 and its absolute expression
+};
+
+__device__ __forceinline__ K32 fd_K32(const double* u, const Geo& g, const Faces<double>& f, long long row, int j,
+                                      int k, int c) {
+    auto at = [&](long long r, int cc) -> float { return (float)u[r * g.n0 + cc]; };
+    const float uP = at(row, c);
+    const float uW = c > 0 ? at(row, c - 1) : 0.f;
+    const float uE = c + 1 < g.n0 ? at(row, c + 1) : 0.f;
+    const float uS = j > 0 ? at(row - 1, c) : 0.f;
+    const float uN = j + 1 < g.n1 ? at(row + 1, c) : 0.f;
+    const float aP = fabsf(uP), aW = fabsf(uW), aE = fabsf(uE), aS = fabsf(uS), aN = fabsf(uN);
+    K32 o;
+    if (f.fx == nullptr) {
+        const float hx2 = (float)g.hx2, hy2 = (float)g.hy2;
+        o.v = hx2 * (2.f * uP - uW - uE) + hy2 * (2.f * uP - uS - uN);
+        o.a = hx2 * (2.f * aP + aW + aE) + hy2 * (2.f * aP + aS + aN);
+        if (g.d == 3) {
+            const float hz2 = (float)g.hz2;
+            const float uD = k > 0 ? at(row - g.n1, c) : 0.f;
+            const float uU = k + 1 < g.n2 ? at(row + g.n1, c) : 0.f;
+            o.v += hz2 * (2.f * uP - uD - uU);
+            o.a += hz2 * (2.f * aP + fabsf(uD) + fabsf(uU));
+        }
+    } else {
+        const long long fxi = row * (g.n0 + 1) + c;
+        const long long fyi = ((long long)k * (g.n1 + 1) + j) * g.n0 + c;
+        const float fW = (float)f.fx[fxi], fE = (float)f.fx[fxi + 1], fS = (float)f.fy[fyi],
+                    fN = (float)f.fy[fyi + g.n0];
+        o.v = fW * (uP - uW) + fE * (uP - uE) + fS * (uP - uS) + fN * (uP - uN);
+        o.a = fW * (aP + aW) + fE * (aP + aE) + fS * (aP + aS) + fN * (aP + aN);
+        if (g.d == 3) {
+            const float uD = k > 0 ? at(row - g.n1, c) : 0.f;
+            const float uU = k + 1 < g.n2 ? at(row + g.n1, c) : 0.f;
+            const long long fzi = ((long long)k * g.n1 + j) * g.n0 + c;
+            const float fD = (float)f.fz[fzi], fU = (float)f.fz[fzi + (long long)g.n1 * g.n0];
+            o.v += fD * (uP - uD) + fU * (uP - uU);
+            o.a += fD * (aP + fabsf(uD)) + fU * (aP + fabsf(uU));
+        }
+    }
+    return o;
+}
+
+static __global__ void __launch_bounds__(kBlock) k_matvec32(Geo g, int nt, Tab tab, double tau, Faces<double> faces,
+                                                     const double* x, double* y, int transpose, double* part,
+                                                     double* absy) {
+    pdl_prologue();
+    __shared__ double wsum[kBlock / kWarp];
+    const long long w = gwarp();
+    const int lane = lane_id();
+    double sq = 0.0;          // sum of squares of this lane's absolute expressions
+    if (w < (long long)(nt + 1) * g.R) {
+        const int n = (int)(w / g.R);
+        const long long row = w % g.R;
+        int j, k;
+        row_jk(g, row, j, k);
+        const int s = tab.s;
+        const long long nx = g.nx;
+        const long long voff = (long long)(nt + 1) * nx;
+        if (n == nt) {   // y_{v,0} (forward) or y_{v,nt} (transpose)
+            const long long base = (transpose ? (long long)nt * nx : 0) + row * g.n0;
+            for (int c = lane; c < g.n0; c += kWarp) {
+                const float v = (float)x[base + c];
+                y[base + c] = (double)v;
+                if (absy) absy[base + c] = (double)fabsf(v);
+                sq += (double)v * (double)v;
+            }
+        } else {
+            float tA[kMaxS * kMaxS], tb[kMaxS];
+            for (int i = 0; i < s * s; ++i) tA[i] = (float)(tau * tab.A[i]);
+            for (int i = 0; i < s; ++i) tb[i] = (float)(tau * tab.b[i]);
+            const double* xv = x + (long long)n * nx;
+            for (int c = lane; c < g.n0; c += kWarp) {
+                const long long p = row * g.n0 + c;
+                K32 KV[kMaxS];
+                float Vi[kMaxS];
+                for (int i = 0; i < s; ++i) {
+                    const double* xs = x + voff + ((long long)n * s + i) * nx;
+                    KV[i] = fd_K32(xs, g, faces, row, j, k, c);
+                    Vi[i] = (float)xs[p];
+                }
+                const float xn1 = (float)x[(long long)(n + 1) * nx + p], xn = (float)xv[p];
+                if (!transpose) {
+                    const K32 Kv = fd_K32(xv, g, faces, row, j, k, c);
+                    float acc = xn1 - xn, abs_ = fabsf(xn1) + fabsf(xn);
+                    for (int i = 0; i < s; ++i) {
+                        acc -= tb[i] * Vi[i];
+                        abs_ += fabsf(tb[i]) * fabsf(Vi[i]);
+                    }
+                    y[(long long)(n + 1) * nx + p] = (double)acc;
+                    if (absy) absy[(long long)(n + 1) * nx + p] = (double)abs_;
+                    sq += (double)abs_ * (double)abs_;
+                    for (int i = 0; i < s; ++i) {
+                        float a = Vi[i] + Kv.v, aa = fabsf(Vi[i]) + Kv.a;
+                        for (int q = 0; q < s; ++q) {
+                            a += tA[i * s + q] * KV[q].v;
+                            aa += fabsf(tA[i * s + q]) * KV[q].a;
+                        }
+                        y[voff + ((long long)n * s + i) * nx + p] = (double)a;
+                        if (absy) absy[voff + ((long long)n * s + i) * nx + p] = (double)aa;
+                        sq += (double)aa * (double)aa;
+                    }
+                } else {
+                    float acc = xn - xn1, abs_ = fabsf(xn) + fabsf(xn1);
+                    for (int i = 0; i < s; ++i) {
+                        acc += KV[i].v;
+                        abs_ += KV[i].a;
+                    }
+                    y[(long long)n * nx + p] = (double)acc;
+                    if (absy) absy[(long long)n * nx + p] = (double)abs_;
+                    sq += (double)abs_ * (double)abs_;
+                    for (int i = 0; i < s; ++i) {
+                        float a = Vi[i] - tb[i] * xn1, aa = fabsf(Vi[i]) + fabsf(tb[i]) * fabsf(xn1);
+                        for (int q = 0; q < s; ++q) {
+                            a += tA[q * s + i] * KV[q].v;
+                            aa += fabsf(tA[q * s + i]) * KV[q].a;
+                        }
+                        y[voff + ((long long)n * s + i) * nx + p] = (double)a;
+                        if (absy) absy[voff + ((long long)n * s + i) * nx + p] = (double)aa;
+                        sq += (double)aa * (double)aa;
+                    }
+                }
+            }
+        }
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) wsum[threadIdx.x / kWarp] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kBlock / kWarp; ++i) t += wsum[i];
+        part[blockIdx.x] = t;
+    }
+}
+
+// Accept or reject the FP32 product of outer iteration k: bound = gamma_d (1 + gamma_d)
+// sqrt(sum part) (the factor 1 + gamma_d covers the rounding of the absolute expression itself),
+// allowed = ell tol ||b|| / (m |g_k|) with ||b|| = bnorm[0] and g_k = gk[0] (the current Givens
+// residual).  flag[0] = 1 keeps the FP32 product (the FP64 launch that follows skips), flag[1]
+// counts the kept products.  One block; the partial sums are added in a fixed order.
+static __global__ void __launch_bounds__(kBlock) k_relax_decide(const double* part, int nblk, double gamma_d,
+                                                         double ell, double tol, int m, const double* bnorm,
+                                                         const double* gk, int* flag) {
+    pdl_prologue();
+    __shared__ double red[kBlock];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += kBlock) t += part[i];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = kBlock / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double bound = gamma_d * (1.0 + gamma_d) * sqrt(red[0]);
+        const double g = fabs(gk[0]);
+        const double allowed = g > 0.0 ? ell * tol * bnorm[0] / ((double)m * g) : 0.0;
+        const int keep = isfinite(bound) && bound <= allowed ? 1 : 0;
+        flag[0] = keep;
+        flag[1] += keep;
     }
 }
 

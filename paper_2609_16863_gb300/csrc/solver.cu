@@ -210,6 +210,20 @@ static bool is_device_ptr(const void* p) {
 }
 
 // ---------------------------------------------------------------------------
+// relax_matvec: finite and >= 0; > 0 needs the FD product (the FP32 kernel) and right
+// preconditioning (the allowance is stated for the right-preconditioned residual).
+static aao_status check_relax(double ell, bool q1, int precond_side) {
+    if (!(ell >= 0.0) || !std::isfinite(ell)) {
+        set_error("relax_matvec must be finite and >= 0");
+        return AAO_ERR_ARG;
+    }
+    if (ell > 0.0 && (q1 || precond_side != 0)) {
+        set_error("relax_matvec > 0 needs finite differences and right preconditioning");
+        return AAO_ERR_UNSUPPORTED;
+    }
+    return AAO_OK;
+}
+
 static aao_status validate(const aao_grid* grid, double tau, int nt, const aao_tableau* tab,
                            const aao_options* o) {
     if (!grid || !tab || !o) {
@@ -281,7 +295,7 @@ static aao_status validate(const aao_grid* grid, double tau, int nt, const aao_t
                   "(aao_rk_grad_kappa with accumulate)");
         return AAO_ERR_UNSUPPORTED;
     }
-    return AAO_OK;
+    return check_relax(o->relax_matvec, grid->disc == AAO_DISC_Q1, o->precond_side);
 }
 
 static void resolve_defaults(aao_options* o) {
@@ -396,6 +410,8 @@ static aao_status setup_handle(Handle* h, const aao_grid* grid, double tau, int 
     if (h->opt.precond_side == 1) AAO_TRY(ar.alloc(&h->bt, (size_t)h->nst));   // left: P^{-1} b, no Z basis
     else AAO_TRY(ar.alloc(&h->Z, (size_t)m * h->nst));
     AAO_TRY(ar.alloc(&h->w, (size_t)h->nst));
+    AAO_TRY(ar.alloc(&h->relax_part, (size_t)blocks_for_rows((long long)(nt + 1) * h->g.R)));
+    AAO_TRY(ar.alloc(&h->relax_flag, 2));
     AAO_TRY(ar.alloc(&h->r, (size_t)h->nst));
     AAO_TRY(ar.alloc(&h->rhs, (size_t)h->nst));
     AAO_TRY(ar.alloc(&h->xs, (size_t)h->nst));
@@ -437,7 +453,29 @@ static aao_status matvec_dev(Handle* h, const double* x, double* y, const double
     }
     bytes_hint(8.0 * h->nst * (rhs ? 3 : 2));
     launch(k_matvec, blocks_for_rows((long long)(h->nt + 1) * g.R), kBlock, 0, h->stream, 
-        g, h->nt, h->tab, h->tau, h->faces64, x, y, rhs, transpose);
+        g, h->nt, h->tab, h->tau, h->faces64, x, y, rhs, transpose, (const int*)nullptr);
+    AAO_LAUNCH_CHECK();
+    return AAO_OK;
+}
+
+// y = A z_k (transpose: A^T z_k) of outer iteration k with the relaxed precision of
+// aao_options.relax_matvec: the FP32 product and its error bound, the decision on the device
+// (gv[k] is the current least-squares residual |g_k|, beta[1] = ||b||), and the FP64 product in
+// its place when the bound is above the allowance.  No host synchronisation.
+static aao_status matvec_relaxed(Handle* h, const double* z, double* y, int k, int transpose) {
+    NvtxRange range_("aao.matvec_relaxed");
+    const Geo& g = h->g;
+    const unsigned nblk = blocks_for_rows((long long)(h->nt + 1) * g.R);
+    bytes_hint(8.0 * h->nst * 2);
+    launch(k_matvec32, nblk, kBlock, 0, h->stream, g, h->nt, h->tab, h->tau, h->faces64, z, y, transpose,
+           h->relax_part, (double*)nullptr);
+    const double gam = (double)kRelaxDepth * 0x1p-24 / (1.0 - (double)kRelaxDepth * 0x1p-24);
+    launch(k_relax_decide, 1, kBlock, 0, h->stream, (const double*)h->relax_part, (int)nblk, gam,
+           h->opt.relax_matvec, h->opt.tol, h->m, (const double*)(h->beta + 1), (const double*)(h->gv + k),
+           h->relax_flag);
+    bytes_hint(8.0 * h->nst * 2);
+    launch(k_matvec, nblk, kBlock, 0, h->stream, g, h->nt, h->tab, h->tau, h->faces64, z, y, (const double*)nullptr,
+           transpose, (const int*)h->relax_flag);
     AAO_LAUNCH_CHECK();
     return AAO_OK;
 }
@@ -484,6 +522,7 @@ static aao_status fgmres(Handle* h, const double* b, double* x, int x0_given, in
     memset(&loc, 0, sizeof(loc));
     h->P->t_theta_ms = h->P->t_schur_ms = 0.f;
     h->P->reset_inner_its();
+    AAO_CUDA_TRY(cudaMemsetAsync(h->relax_flag, 0, 2 * sizeof(int), st));
     AAO_TRY(norm_dev(h, b, h->beta + 1));
     double bnorm = 0.0;
     AAO_CUDA_TRY(cudaMemcpyAsync(&bnorm, h->beta + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -536,7 +575,8 @@ static aao_status fgmres(Handle* h, const double* b, double* x, int x0_given, in
                 double* Vk = h->V + (long long)k * nst;
                 double* Zk = h->Z + (long long)k * nst;
                 AAO_TRY(h->P->apply(Vk, Zk, transpose));
-                AAO_TRY(matvec_dev(h, Zk, h->w, nullptr, transpose));
+                if (h->opt.relax_matvec > 0.0) AAO_TRY(matvec_relaxed(h, Zk, h->w, k, transpose));
+                else AAO_TRY(matvec_dev(h, Zk, h->w, nullptr, transpose));
                 {
                     NvtxRange ortho_("aao.orthogonalize");
                     Vec<double> none{};
@@ -587,6 +627,11 @@ static aao_status fgmres(Handle* h, const double* b, double* x, int x0_given, in
         }
     }
     AAO_CUDA_TRY(cudaStreamSynchronize(st));
+    {
+        int rf[2] = {0, 0};
+        AAO_CUDA_TRY(cudaMemcpy(rf, h->relax_flag, sizeof(rf), cudaMemcpyDeviceToHost));
+        loc.relaxed_matvecs = rf[1];
+    }
     loc.inner_its_total = h->P->inner_its();
     loc.t_theta_ms = h->P->t_theta_ms;
     loc.t_schur_ms = h->P->t_schur_ms;
@@ -813,6 +858,7 @@ void aao_rk_default_options(aao_options* o) {
     o->stream = nullptr;
     o->mgrit_m = 0;
     o->precond_side = 0;
+    o->relax_matvec = 0.0;
 }
 
 const char* aao_rk_last_error(void) { return get_error(); }
@@ -935,6 +981,7 @@ aao_status aao_rk_set_options(aao_rk_handle hh, const aao_options* o) {
                   "fixed at set-up");
         return AAO_ERR_ARG;
     }
+    AAO_TRY(check_relax(o->relax_matvec, hh->h.q1 != 0, c.precond_side));
     aao_options n = *o;
     n.inner_maxit = c.inner_maxit;
     if (n.inner_tol < 0.0) n.inner_tol = c.inner_tol;
@@ -980,6 +1027,26 @@ static aao_status matvec_api(aao_rk_handle hh, const double* x, double* y, int t
 }
 
 aao_status aao_rk_matvec(aao_rk_handle hh, const double* x, double* y) { return matvec_api(hh, x, y, 0); }
+
+aao_status aao_rk_matvec_relaxed(aao_rk_handle hh, const double* x, double* y, double* absy, int transpose) {
+    H_CHECK(hh);
+    Handle* h = &hh->h;
+    if (!is_device_ptr(x) || !is_device_ptr(y) || !is_device_ptr(absy)) {
+        set_error("x, y and absy must be device arrays");
+        return AAO_ERR_ARG;
+    }
+    if (h->q1) {
+        set_error("the FP32 relaxed product is built for finite differences");
+        return AAO_ERR_UNSUPPORTED;
+    }
+    const unsigned nblk = blocks_for_rows((long long)(h->nt + 1) * h->g.R);
+    bytes_hint(8.0 * h->nst * 3);
+    launch(k_matvec32, nblk, kBlock, 0, h->stream, h->g, h->nt, h->tab, h->tau, h->faces64, x, y, transpose ? 1 : 0,
+           h->relax_part, absy);
+    AAO_LAUNCH_CHECK();
+    AAO_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return AAO_OK;
+}
 aao_status aao_rk_matvec_transpose(aao_rk_handle hh, const double* x, double* y) { return matvec_api(hh, x, y, 1); }
 
 static aao_status precond_api(aao_rk_handle hh, const double* r, double* z, int transpose) {

@@ -45,12 +45,44 @@ def test_struct_layouts_match_header_sizes():
     # sizes follow the C layout rules on every 64-bit target this builds for
     from paper_2609_16863_gb300 import _lib
     assert ctypes.sizeof(_lib.aao_tableau) == 4 + 4 + 8 * 64 + 8 * 8 + 8 * 8
-    assert ctypes.sizeof(_lib.aao_info) == 4 + 4 + 8 + 8 + 4 + 4 + 8 * 3 + 4 + 4 + 8 * 128
+    # outer_its, (pad), inner_its_total, rel_res, converged, (pad), 3 times, n_history, (pad),
+    # history[128], relaxed_matvecs, (pad)
+    assert ctypes.sizeof(_lib.aao_info) == 4 + 4 + 8 + 8 + 4 + 4 + 8 * 3 + 4 + 4 + 8 * 128 + 4 + 4
     # tol, restart, maxit, inner_maxit, (pad), inner_tol, mg_cycles, mg_pre, mg_post, (pad), mg_omega,
-    # cheb_steps, prec_P, prec_Pint, ckpt_every, stream, mgrit_m, precond_side
-    assert ctypes.sizeof(_lib.aao_options) == 8 + 4 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 4 + 8 + 4 * 4 + 8 + 4 + 4
+    # cheb_steps, prec_P, prec_Pint, ckpt_every, stream, mgrit_m, precond_side, relax_matvec
+    assert ctypes.sizeof(_lib.aao_options) == 8 + 4 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 4 + 8 + 4 * 4 + 8 + 4 + 4 + 8
     assert _lib.aao_options.precond_side.offset == 84
     assert _lib.aao_options.mgrit_m.offset == 80
+    assert _lib.aao_options.relax_matvec.offset == 88
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every field offset and struct size of the ctypes binding equals what a C compiler gives for
+    include/aao_rk.h (the header and the binding cannot drift apart)."""
+    import shutil
+    import subprocess
+    from paper_2609_16863_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [_lib.aao_grid, _lib.aao_tableau, _lib.aao_options, _lib.aao_info]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "aao_rk.h"', 'int main(void) {']
+    for st in structs:
+        lines.append(f'printf("%zu\\n", sizeof({st.__name__}));')
+        for name, *_ in st._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({st.__name__}, {name}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for st in structs:
+        want.append(ctypes.sizeof(st))
+        want += [getattr(st, name).offset for name, *_ in st._fields_]
+    assert got == want
 
 
 def test_setup_rejects_bad_arguments_without_gpu(lib):
@@ -116,7 +148,25 @@ SETUP_BAD = [
     ("fp16_bf16", None, b"16-bit"), ("null_grid", None, b"null"), ("null_out", None, b"null output"),
     ("opts.mgrit_m", 1, b"mgrit_m"), ("opts.mgrit_m", 3, b"mgrit_m"), ("opts.mgrit_m", -2, b"mgrit_m"),
     ("opts.precond_side", 2, b"precond_side"),
+    ("opts.relax_matvec", -1.0, b"relax_matvec"), ("opts.relax_matvec", float("nan"), b"relax_matvec"),
+    ("opts.relax_matvec", float("inf"), b"relax_matvec"),
 ]
+
+
+@pytest.mark.parametrize("case", ["q1", "left"])
+def test_relaxed_product_needs_fd_and_right_preconditioning(lib, case):
+    """The FP32 relaxed product is built for finite differences, and its allowance is stated for the
+    right-preconditioned residual: other combinations are refused at set-up, before device work."""
+    L, g, t, o = _valid_setup_args()
+    o.relax_matvec = 1.0
+    if case == "q1":
+        g.disc = 1
+    else:
+        o.precond_side = 1
+    out = ctypes.c_void_p()
+    st = L.aao_rk_setup(ctypes.byref(g), 0.1, 4, ctypes.byref(t), ctypes.byref(o), ctypes.byref(out))
+    assert st == -8 and not out.value
+    assert b"relax_matvec" in L.aao_rk_last_error()
 
 
 @pytest.mark.parametrize("what,value,words", SETUP_BAD)
