@@ -68,6 +68,10 @@ def parse():
     p.add_argument("--theta-case", action="store_true",
                    help="profiler case: --steps batched Theta_tilde solves over all 128 time blocks of the "
                         "benchmark grid (256x256, s=3, P_tilde FP32; vectors of 100 MB, larger than L2)")
+    p.add_argument("--batch-case", action="store_true",
+                   help="profiler case: batched Theta_tilde solves of 1..32 time blocks of the benchmark grid "
+                        "(256x256, s=3, P_tilde --prec): ms per solve and event-timed k_cluster_mg launches per "
+                        "batch size (one thread-block cluster per item)")
     p.add_argument("--matvec-case", action="store_true",
                    help="profiler case: --steps FP64 all-at-once matvecs at the benchmark size (269 MB vectors)")
     p.add_argument("--mgrit-m", type=int, default=-1,
@@ -434,6 +438,41 @@ def theta_case(args):
     S.close()
 
 
+def batch_case(args):
+    """Batched Theta_tilde solves of B = 1..32 time blocks on the benchmark grid: up to 32 items run one
+    thread-block cluster per item (16 CTAs for fewer than 8 items, 8 CTAs from 8 on), so the launch
+    time of k_cluster_mg against B shows how many clusters are resident at once."""
+    import ctypes as C
+    import torch
+    from paper_2609_16863_gb300 import Solver, radau_iia, _lib
+    w = workload(False)
+    S = Solver(w.n, w.T, 32, tableau=radau_iia(w.s), prec_P=args.prec, inner_maxit=3, inner_tol=1e-3, restart=1)
+    lib = S._lib
+    g = torch.Generator(device="cuda:0").manual_seed(6)
+    rows = {}
+    for B in (1, 2, 4, 7, 8, 12, 14, 16, 24, 32):
+        n = B * w.s * S.nx
+        r = torch.randn(n, dtype=torch.float64, device="cuda:0", generator=g)
+        z = torch.zeros_like(r)
+        for _ in range(max(args.warmup, 1)):
+            S.inner_solve(B, r, z)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(max(args.steps, 1)):
+            S.inner_solve(B, r, z)
+        e1.record()
+        torch.cuda.synchronize()
+        _lib.check(lib.aao_rk_profile_begin(b"k_cluster_mg"))
+        S.inner_solve(B, r, z)
+        nl, pms, pby = C.c_longlong(), C.c_double(), C.c_double()
+        _lib.check(lib.aao_rk_profile_end(C.byref(nl), C.byref(pms), C.byref(pby)))
+        rows[B] = {"ms_per_solve": round(e0.elapsed_time(e1) / max(args.steps, 1), 3),
+                   "cluster_launches": nl.value, "us_per_cluster_launch": round(1e3 * pms.value / max(1, nl.value), 1)}
+    print(json.dumps({"case": "batched theta fd2d_n256_radau3", "prec": args.prec, "batches": rows}))
+    S.close()
+
+
 def matvec_case(args):
     """The FP64 all-at-once matvec y = A x at the benchmark size."""
     import torch
@@ -493,6 +532,9 @@ def main():
         return
     if args.matvec_case:
         matvec_case(args)
+        return
+    if args.batch_case:
+        batch_case(args)
         return
     import torch
     import torch.distributed as dist

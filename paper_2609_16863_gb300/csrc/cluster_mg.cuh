@@ -39,6 +39,7 @@ namespace aao {
 constexpr int kClMax = 16;            // CTAs per cluster (16 needs the non-portable size)
 constexpr int kClThreads = 512;
 constexpr int kClMaxBatch = 32;       // batches of at most this many items run one cluster per item
+constexpr int kClBatch8 = 8;          // batches of at least this many items take the 8-CTA plan
 
 template <class SI> struct ClCtx {
     using A = typename PT<SI>::A;
@@ -63,6 +64,10 @@ template <class SI> struct ClCtx {
     const SI* sten[kMaxLevels];
     const float* sten_sc[kMaxLevels];
     const A* Dinv;
+    // lean plans (a cluster of 8 for batches, where the full layout does not fit shared memory):
+    int sten_global[kMaxLevels];          // 1: level l's stencil is read from global memory (L2), not staged
+    int dinv_global;                      // 1: the rows of A_c^{-1} are read from global memory
+    int w0_const;                         // 1: level 0's omega / a_PP is one scalar (FD, kappa = 1)
 };
 
 // This CTA's share of a distributed level.
@@ -80,7 +85,8 @@ template <class A> struct ClL {
     unsigned magic;
     A* X;                     // buffer 0 at (row -1, column -1); buffer k at X + k*xs; (lr, c) at (lr+1)*ld + c+1
     const A* S;               // stored stencil (component stride cs = maxr*n0); nullptr: FD level 0
-    const A* W;               // omega / a_PP (index lr*n0 + c)
+    const A* W;               // omega / a_PP (index lr*n0 + c); nullptr: the scalar w0
+    A w0;
     A *pu0, *pu1, *pu2;       // neighbours' ghost rows (see ClLev)
     A *pd0, *pd1, *pd2;
     A sigma, c, hx2, hy2;
@@ -107,6 +113,7 @@ template <class SI> struct ClShared {
     ClCtx<SI> t;
     ClLev<typename PT<SI>::A> lv[kMaxLevels];
     ClL<typename PT<SI>::A> lev[kMaxLevels];
+    typename PT<SI>::A w0;    // level 0's omega / a_PP where it is one scalar (w0_const)
     int rank;
 };
 
@@ -157,8 +164,17 @@ __device__ __forceinline__ ClL<typename PT<SI>::A> cl_level(const ClShared<SI>& 
     v.a = dist ? S.lv[l].a : 0;
     v.nr = dist ? S.lv[l].nr : v.n1;
     v.X = sm + t.off[l];
-    v.S = (l == 0 && t.fine0) || t.soff[l] < 0 ? nullptr : sm + t.soff[l];
+    if ((l == 0 && t.fine0) || (t.soff[l] < 0 && !t.sten_global[l])) {
+        v.S = nullptr;
+    } else if (t.sten_global[l]) {
+        // the level's stencil in global memory: component stride n_x, rows from this CTA's first
+        v.S = reinterpret_cast<const A*>(t.sten[l]) + (long long)v.a * v.n0;
+        v.cs = (int)t.g[l].nx;
+    } else {
+        v.S = sm + t.soff[l];
+    }
     v.W = t.woff[l] < 0 ? nullptr : sm + t.woff[l];
+    v.w0 = S.w0;
     v.pu0 = dist ? S.lv[l].pu[0] : nullptr;
     v.pu1 = dist ? S.lv[l].pu[1] : nullptr;
     v.pu2 = dist ? S.lv[l].pu[2] : nullptr;
@@ -217,11 +233,12 @@ __device__ __forceinline__ void cl_sweep(const ClL<A>& vin, int kin, bool zero, 
         const int c = p - lr * n0;
         const A bp = *v.el(2, lr, c);
         A val;
+        const A wp = v.W ? v.W[p] : v.w0;
         if (zero) {
-            val = v.W[p] * bp;
+            val = wp * bp;
         } else {
             const A* xm = v.el(kin, lr, c);
-            val = xm[0] + v.W[p] * (bp - cl_apply(v, p, lr, c, xm));
+            val = xm[0] + wp * (bp - cl_apply(v, p, lr, c, xm));
         }
         v.put(1 - kin, lr, c, val);
     }
@@ -387,6 +404,7 @@ __device__ __forceinline__ void cl_stage_async(const ClCtx<SI>& t, int rank, int
         for (int p = tid; p < nfy; p += nthr) cp_async4(sm + t.fyoff + p, fy + p);
     }
     for (int l = t.fine0 ? 1 : 0; l < L - 1; ++l) {
+        if (t.sten_global[l]) continue;
         const Geo& gl = t.g[l];
         const bool dist = l < T;
         const int al = dist ? t.rlo[l][rank] : 0;
@@ -396,7 +414,7 @@ __device__ __forceinline__ void cl_stage_async(const ClCtx<SI>& t, int rank, int
         for (int q = 0; q < 9; ++q)
             for (int p = tid; p < npl; p += nthr) cp_async4(sm + t.soff[l] + q * cs + p, src + (long long)q * gl.nx + p);
     }
-    {
+    if (!t.dinv_global) {
         const int nc = (int)t.g[L - 1].nx;
         const int n = (t.cs[rank + 1] - t.cs[rank]) * nc;
         const float* src = reinterpret_cast<const float*>(t.Dinv) + (long long)t.cs[rank] * nc;
@@ -405,7 +423,7 @@ __device__ __forceinline__ void cl_stage_async(const ClCtx<SI>& t, int rank, int
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     // Jacobi weights omega / a_PP from the staged faces / stencil centres
-    if (t.fine0) {
+    if (t.fine0 && !t.w0_const) {
         const int np0 = nr * g.n0;
         for (int p = tid; p < np0; p += nthr) {
             float kd;
@@ -427,7 +445,12 @@ __device__ __forceinline__ void cl_stage_async(const ClCtx<SI>& t, int rank, int
         const int al = dist ? t.rlo[l][rank] : 0;
         const int npl = dist ? (t.rlo[l][rank + 1] - al) * gl.n0 : (int)gl.nx;
         const int cs = t.maxr[l] * gl.n0;
-        for (int p = tid; p < npl; p += nthr) sm[t.woff[l] + p] = t.omega / sm[t.soff[l] + 4 * cs + p];
+        if (t.sten_global[l]) {
+            const float* ctr = reinterpret_cast<const float*>(t.sten[l]) + 4 * gl.nx + (long long)al * gl.n0;
+            for (int p = tid; p < npl; p += nthr) sm[t.woff[l] + p] = t.omega / ctr[p];
+        } else {
+            for (int p = tid; p < npl; p += nthr) sm[t.woff[l] + p] = t.omega / sm[t.soff[l] + 4 * cs + p];
+        }
     }
 }
 
@@ -504,6 +527,12 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
             rowtab[i] = r == rank ? q : cl_map(q, (unsigned)r);
         }
     }
+    if (tid == 0 && t.w0_const) {
+        // the formula of the staged weights (FD, kappa = 1: the same at every point)
+        const Geo& g = t.g[0];
+        const A kd = A(2) * A(g.hx2) + A(2) * A(g.hy2);
+        S.w0 = t.omega / (t.sigma + t.c * kd);
+    }
     __syncthreads();
     if (tid < L) S.lev[tid] = cl_level(S, sm, tid);
     if constexpr (std::is_same<SI, float>::value && std::is_same<typename PT<SI>::A, float>::value) {
@@ -536,7 +565,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
                     if (p < nb0) B0[(lr + 1) * ld0 + p - (lr + 1) * g.n0 + 1] = v[u];
                 }
             }
-            if (t.fine0) {
+            if (t.fine0 && !t.w0_const) {
                 const int w = g.n0 + 1;
                 if (t.has_faces) {
                     const int nfx = nr * w, nfy = (nr + 1) * g.n0;
@@ -585,6 +614,12 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
                 const int npl = dist ? (t.rlo[l][rank + 1] - al) * gl.n0 : (int)gl.nx;
                 const int cs = t.maxr[l] * gl.n0;
                 const SI* src = t.sten[l] + (long long)al * gl.n0;
+                if (t.sten_global[l]) {
+                    // read in place (planned only where the storage type is the arithmetic type)
+                    for (int p = tid; p < npl; p += nthr)
+                        sm[t.woff[l] + p] = t.omega / reinterpret_cast<const A*>(src)[4 * gl.nx + p];
+                    continue;
+                }
                 for (int p = tid; p < npl; p += nthr) {
                     A v[9];
     #pragma unroll
@@ -597,7 +632,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
                     sm[t.woff[l] + p] = t.omega / v[4];
                 }
             }
-            {
+            if (!t.dinv_global) {
                 const int nc = (int)t.g[L - 1].nx;
                 const int n = (t.cs[rank + 1] - t.cs[rank]) * nc;
                 const A* src = t.Dinv + (long long)t.cs[rank] * nc;
@@ -662,7 +697,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
                 bvec[p] = *v.el(2, lr, p - lr * v.n0);
             }
             __syncthreads();
-            const A* Di = sm + t.dinv_off;
+            const A* Di = t.dinv_global ? t.Dinv + (long long)t.cs[rank] * nc : sm + t.dinv_off;
             const int lo = t.cs[rank], hi = t.cs[rank + 1];
             const int w = tid >> 5, lane = tid & 31, nw = nthr >> 5;
             for (int p = lo + w; p < hi; p += nw) {

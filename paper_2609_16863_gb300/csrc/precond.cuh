@@ -78,9 +78,13 @@ class Precond : public PrecondBase {
     Tail tails[2];                 // [0]: B == 1, [1]: B > 1
     int tail_threads = 1024;
     // Cluster-resident shifted solves for single 2D items (the Schur sweep).
-    int cl_C = 0;                  // CTAs per cluster; 0: not used for this problem
-    size_t cl_smem = 0;
-    ClCtx<SI>* cl_ctx = nullptr;   // device, one context per stage
+    int cl_C = 0;                  // CTAs per cluster of the single-item plan; 0: no cluster plan
+    struct ClPlan {
+        int C = 0;                 // CTAs per cluster; 0: none
+        size_t smem = 0;
+        ClCtx<SI>* ctx = nullptr;  // device, one context per stage
+    };
+    ClPlan clp[2];                 // [0] single items, [1] batches of at least kClBatch8 items
     int* hact = nullptr;           // pinned mirror of activeh (profiling)
 
     cudaStream_t cur_stream = nullptr;     // stream of the next launch (capture stream while capturing)
@@ -471,118 +475,154 @@ class Precond : public PrecondBase {
         return AAO_OK;
     }
 
-    // Plan the cluster-resident shifted solve: 2D, at least one level above the
-    // coarsest, everything of a CTA's rows within its shared memory, and one
-    // cluster of 16 (else 8) CTAs co-resident on the device.
+    // Plan the cluster-resident shifted solve: 2D, at least one level above the coarsest, every
+    // CTA owning rows of every distributed level, its share within shared memory, and the cluster
+    // co-resident on the device.  Two plans: one for single items (16 CTAs where the full layout
+    // fits, else 8) and one for batches (8 CTAs, so that about twice as many items run at once:
+    // at 256^2 only 7 clusters of 16 are resident).  A plan that does not fit shared memory is made
+    // lean step by step: level 0's Jacobi weight as a scalar (FD, kappa = 1), the rows of A_c^{-1}
+    // read from global memory, then the coarse stencils read from global memory (L2) from level 1
+    // on (only where the storage type is the arithmetic type).  Lean plans give the same values.
+    bool plan_cluster(int C, int lean, long long dyn_max, ClCtx<SI>& t, long long& bytes) {
+        const Geo& g0 = h->g;
+        const int T = L - 1;
+        if (g0.n1 < C) return false;
+        const bool fine0 = !h->q1;
+        const bool faces = fine0 && h->has_kappa;
+        const bool same = std::is_same<SI, A>::value;
+        const bool w0c = lean >= 1 && fine0 && !faces;
+        if (lean >= 2 && !same) return false;
+        std::memset(&t, 0, sizeof(t));
+        t.C = C;
+        t.L = L;
+        t.T = T;
+        t.cycles = h->opt.mg_cycles;
+        t.nu1 = h->opt.mg_pre;
+        t.nu2 = h->opt.mg_post;
+        t.omega = (A)h->opt.mg_omega;
+        t.sigma = A(1);
+        t.fine0 = fine0 ? 1 : 0;
+        t.has_faces = faces ? 1 : 0;
+        t.fx = facesA.fx;
+        t.fy = facesA.fy;
+        t.w0_const = w0c ? 1 : 0;
+        t.dinv_global = lean >= 1 ? 1 : 0;
+        for (int l = 1; l < L - 1; ++l) t.sten_global[l] = (lean >= 3 || (lean == 2 && l == 1)) ? 1 : 0;
+        long long o = 0;
+        auto take = [&](long long n) {
+            long long at = o;
+            o += (n + 3) / 4 * 4;
+            return (int)at;
+        };
+        // Every CTA must own at least one row of every distributed level: a CTA whose coarse
+        // range is empty would interpolate from coarse ghost rows that no neighbour stores to
+        // (neighbours push only to non-empty CTAs).  Grids with few rows for their width
+        // (e.g. 120 x 17 at C = 16) fail this and take a smaller cluster or the level kernels.
+        bool nonempty = true;
+        for (int l = 0; l < L; ++l) {
+            const Geo& gl = lev[l].g;
+            t.g[l] = gl;
+            t.magic[l] = (unsigned)((4294967296ULL + (unsigned long long)gl.n0 - 1) / (unsigned long long)gl.n0);
+            if (l < T) {
+                for (int r = 0; r <= C; ++r)
+                    t.rlo[l][r] = l == 0 ? (int)((long long)r * gl.n1 / C) : t.rlo[l - 1][r] / 2;
+                int mr = 0;
+                for (int r = 0; r < C; ++r) {
+                    mr = std::max(mr, t.rlo[l][r + 1] - t.rlo[l][r]);
+                    nonempty = nonempty && t.rlo[l][r + 1] > t.rlo[l][r];
+                }
+                t.maxr[l] = std::max(mr, 1);
+            } else {
+                t.maxr[l] = gl.n1;
+            }
+            t.off[l] = take(3LL * (t.maxr[l] + 2) * (gl.n0 + 2));
+        }
+        if (!nonempty) return false;
+        for (int l = 0; l < L; ++l) {
+            t.soff[l] = t.woff[l] = -1;
+            if ((l >= 1 || !fine0) && l < L - 1 && !t.sten_global[l]) t.soff[l] = take(9LL * t.maxr[l] * lev[l].g.n0);
+            if (l < L - 1 && !(l == 0 && w0c)) t.woff[l] = take((long long)t.maxr[l] * lev[l].g.n0);
+        }
+        t.fxoff = t.fyoff = -1;
+        if (faces) {
+            t.fxoff = take((long long)t.maxr[0] * (g0.n0 + 1));
+            t.fyoff = take((long long)(t.maxr[0] + 1) * g0.n0);
+        }
+        const long long ncst = lev[L - 1].g.nx;
+        int msl = 0;
+        for (int r = 0; r <= C; ++r) t.cs[r] = (int)((long long)r * ncst / C);
+        for (int r = 0; r < C; ++r) msl = std::max(msl, t.cs[r + 1] - t.cs[r]);
+        t.dinv_off = t.dinv_global ? -1 : take((long long)msl * ncst);
+        t.rowtab_off = take(((long long)lev[T - 1].g.n1 * (long long)sizeof(void*) + sizeof(A) - 1) / sizeof(A));
+        bytes = o * (long long)sizeof(A);
+        if (bytes > dyn_max) return false;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C);
+        cfg.blockDim = dim3(kClThreads);
+        cfg.dynamicSmemBytes = (size_t)bytes;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_cluster_mg<SI>, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    }
+
+    aao_status store_cluster_plan(ClPlan& pl, const ClCtx<SI>& t, long long bytes) {
+        ClCtx<SI> hc[kMaxS];
+        for (int i = 0; i < h->s; ++i) {
+            hc[i] = t;
+            hc[i].c = (A)(h->tau * h->D[i]);
+            for (int l = 0; l < L; ++l) {
+                hc[i].sten[l] = lev[l].sten[i];
+                hc[i].sten_sc[l] = lev[l].sten_sc[i];
+            }
+            hc[i].Dinv = Dinv[i];
+        }
+        AAO_TRY(ar.alloc(&pl.ctx, (size_t)h->s));
+        AAO_CUDA_TRY(cudaMemcpy(pl.ctx, hc, sizeof(ClCtx<SI>) * h->s, cudaMemcpyHostToDevice));
+        pl.C = t.C;
+        pl.smem = (size_t)bytes;
+        return AAO_OK;
+    }
+
     aao_status build_cluster(int optin) {
         cl_C = 0;
+        clp[0] = clp[1] = ClPlan{};
         const Geo& g0 = h->g;
         if (g0.d != 2 || L < 2) return AAO_OK;
-        const int T = L - 1;
         cudaFuncAttributes fa;
         AAO_CUDA_TRY(cudaFuncGetAttributes(&fa, k_cluster_mg<SI>));
         const long long dyn_max = (long long)optin - (long long)fa.sharedSizeBytes;
         if (dyn_max <= 0) return AAO_OK;
         AAO_CUDA_TRY(cudaFuncSetAttribute(k_cluster_mg<SI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max));
         AAO_CUDA_TRY(cudaFuncSetAttribute(k_cluster_mg<SI>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        const bool fine0 = !h->q1;
-        const bool faces = fine0 && h->has_kappa;
+        ClCtx<SI> t;
+        long long bytes = 0;
+        // single items: the full layout first (staged once per launch), 16 CTAs before 8
+        bool found = false;
         for (int C : {16, 8}) {
-            if (g0.n1 < C) continue;
-            ClCtx<SI> t;
-            std::memset(&t, 0, sizeof(t));
-            t.C = C;
-            t.L = L;
-            t.T = T;
-            t.cycles = h->opt.mg_cycles;
-            t.nu1 = h->opt.mg_pre;
-            t.nu2 = h->opt.mg_post;
-            t.omega = (A)h->opt.mg_omega;
-            t.sigma = A(1);
-            t.fine0 = fine0 ? 1 : 0;
-            t.has_faces = faces ? 1 : 0;
-            t.fx = facesA.fx;
-            t.fy = facesA.fy;
-            long long o = 0;
-            auto take = [&](long long n) {
-                long long at = o;
-                o += (n + 3) / 4 * 4;
-                return (int)at;
-            };
-            // Every CTA must own at least one row of every distributed level: a CTA whose coarse
-            // range is empty would interpolate from coarse ghost rows that no neighbour stores to
-            // (neighbours push only to non-empty CTAs).  Grids with few rows for their width
-            // (e.g. 120 x 17 at C = 16) fail this and take a smaller cluster or the level kernels.
-            bool nonempty = true;
-            for (int l = 0; l < L; ++l) {
-                const Geo& gl = lev[l].g;
-                t.g[l] = gl;
-                t.magic[l] = (unsigned)((4294967296ULL + (unsigned long long)gl.n0 - 1) / (unsigned long long)gl.n0);
-                if (l < T) {
-                    for (int r = 0; r <= C; ++r)
-                        t.rlo[l][r] = l == 0 ? (int)((long long)r * gl.n1 / C) : t.rlo[l - 1][r] / 2;
-                    int mr = 0;
-                    for (int r = 0; r < C; ++r) {
-                        mr = std::max(mr, t.rlo[l][r + 1] - t.rlo[l][r]);
-                        nonempty = nonempty && t.rlo[l][r + 1] > t.rlo[l][r];
-                    }
-                    t.maxr[l] = std::max(mr, 1);
-                } else {
-                    t.maxr[l] = gl.n1;
-                }
-                t.off[l] = take(3LL * (t.maxr[l] + 2) * (gl.n0 + 2));
-            }
-            if (!nonempty) continue;
-            for (int l = 0; l < L; ++l) {
-                t.soff[l] = t.woff[l] = -1;
-                if ((l >= 1 || !fine0) && l < L - 1) t.soff[l] = take(9LL * t.maxr[l] * lev[l].g.n0);
-                if (l < L - 1) t.woff[l] = take((long long)t.maxr[l] * lev[l].g.n0);
-            }
-            t.fxoff = t.fyoff = -1;
-            if (faces) {
-                t.fxoff = take((long long)t.maxr[0] * (g0.n0 + 1));
-                t.fyoff = take((long long)(t.maxr[0] + 1) * g0.n0);
-            }
-            const long long ncst = lev[L - 1].g.nx;
-            int msl = 0;
-            for (int r = 0; r <= C; ++r) t.cs[r] = (int)((long long)r * ncst / C);
-            for (int r = 0; r < C; ++r) msl = std::max(msl, t.cs[r + 1] - t.cs[r]);
-            t.dinv_off = take((long long)msl * ncst);
-            t.rowtab_off = take(((long long)lev[T - 1].g.n1 * (long long)sizeof(void*) + sizeof(A) - 1) / sizeof(A));
-            const long long bytes = o * (long long)sizeof(A);
-            if (bytes > dyn_max) continue;
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(C);
-            cfg.blockDim = dim3(kClThreads);
-            cfg.dynamicSmemBytes = (size_t)bytes;
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = (unsigned)C;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            int nclusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclusters, k_cluster_mg<SI>, &cfg) != cudaSuccess || nclusters < 1) {
-                cudaGetLastError();
-                continue;
-            }
-            ClCtx<SI> hc[kMaxS];
-            for (int i = 0; i < h->s; ++i) {
-                hc[i] = t;
-                hc[i].c = (A)(h->tau * h->D[i]);
-                for (int l = 0; l < L; ++l) {
-                    hc[i].sten[l] = lev[l].sten[i];
-                    hc[i].sten_sc[l] = lev[l].sten_sc[i];
-                }
-                hc[i].Dinv = Dinv[i];
-            }
-            AAO_TRY(ar.alloc(&cl_ctx, (size_t)h->s));
-            AAO_CUDA_TRY(cudaMemcpy(cl_ctx, hc, sizeof(ClCtx<SI>) * h->s, cudaMemcpyHostToDevice));
-            cl_C = C;
-            cl_smem = (size_t)bytes;
-            return AAO_OK;
+            for (int lean = 0; lean <= 3 && !found; ++lean) found = plan_cluster(C, lean, dyn_max, t, bytes);
+            if (found) break;
         }
+        if (!found) return AAO_OK;
+        AAO_TRY(store_cluster_plan(clp[0], t, bytes));
+        // batches: 8 CTAs per item, the leanest layout that fits
+        if (clp[0].C == 8) {
+            clp[1] = clp[0];
+        } else {
+            bool fb = false;
+            for (int lean = 0; lean <= 3 && !fb; ++lean) fb = plan_cluster(8, lean, dyn_max, t, bytes);
+            if (fb) AAO_TRY(store_cluster_plan(clp[1], t, bytes));
+        }
+        cl_C = clp[0].C;
         return AAO_OK;
     }
 
@@ -843,9 +883,10 @@ class Precond : public PrecondBase {
     aao_status mg_solve(int stage, int B, const int* act, Vec<SI> b, Vec<SI> out) {
         if (B <= kClMaxBatch && cl_C > 0) {
             // one cluster per item: small batches (single time steps, MGRIT's batched steps)
+            const ClPlan& pl = B >= kClBatch8 && clp[1].C > 0 ? clp[1] : clp[0];
             bytes_hint(2.0 * nact * h->g.nx * sizeof(SI));
-            launch_cluster(k_cluster_mg<SI>, dim3((unsigned)(cl_C * B)), dim3(kClThreads), cl_smem, st(), cl_C,
-                           (const ClCtx<SI>*)(cl_ctx + stage), act, b, out);
+            launch_cluster(k_cluster_mg<SI>, dim3((unsigned)(pl.C * B)), dim3(kClThreads), pl.smem, st(), pl.C,
+                           (const ClCtx<SI>*)(pl.ctx + stage), act, b, out);
             AAO_LAUNCH_CHECK();
             return AAO_OK;
         }

@@ -235,7 +235,10 @@ def test_mixed_precision_solve_error(prec):
 # Grids large enough that the fine levels run level by level and only the coarse
 # levels go through the fused on-chip tail kernel.
 BIG = [((128, 128), 2, "radau", 2, False, "fp64"), ((129, 97), 2, "radau", 3, True, "fp64"),
-       ((40, 36, 44), 2, "gauss", 2, False, "fp64"), ((256, 256), 2, "radau", 3, False, "fp32")]
+       ((40, 36, 44), 2, "gauss", 2, False, "fp64"), ((256, 256), 2, "radau", 3, False, "fp32"),
+       # FP64 at 256^2: the single-item cluster plan is the lean one (level-1 stencil and coarsest
+       # inverse read from L2, a scalar level-0 Jacobi weight)
+       ((256, 256), 2, "radau", 2, False, "fp64")]
 
 
 @pytest.mark.parametrize("ns,nt,method,s,var,prec", BIG)
