@@ -679,7 +679,7 @@ def main():
         ach = r["bytes"] / (r["ms"] * 1e-3) / 1e9 if r["ms"] > 0 else 0.0
         per = r["bytes"] / max(1, r["launches"])
         return {"bound": "hbm", "kernel": r["kernel"], "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": None, "peak_kind": peak_kind + " copy bandwidth, of measured",
+                "frac": ach / peak, "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth, of {peak_kind}",
                 "launches_per_solve": r["launches"], "kernel_ms": r["ms"],
                 "algorithmic_bytes_per_launch": per,
                 "share_of_profiled_time": r["ms"] / total_ms if total_ms > 0 else None}

@@ -40,6 +40,8 @@ constexpr int kClMax = 16;            // CTAs per cluster (16 needs the non-port
 constexpr int kClThreads = 512;
 constexpr int kClMaxBatch = 32;       // batches of at most this many items run one cluster per item
 constexpr int kClBatch8 = 8;          // batches of at least this many items take the 8-CTA plan
+constexpr int kClPad = 4;             // columns before a row's first point (column -1 is the last of them) and
+                                      // after its last (column n0 the first): rows start 16-byte aligned
 
 template <class SI> struct ClCtx {
     using A = typename PT<SI>::A;
@@ -68,6 +70,8 @@ template <class SI> struct ClCtx {
     int sten_global[kMaxLevels];          // 1: level l's stencil is read from global memory (L2), not staged
     int dinv_global;                      // 1: the rows of A_c^{-1} are read from global memory
     int w0_const;                         // 1: level 0's omega / a_PP is one scalar (FD, kappa = 1)
+    int vec[kMaxLevels];                  // 1: level l's sweeps and residual take 16-byte vectors of points
+    unsigned magicv[kMaxLevels];          // ceil(2^32 / (n0_l / points per vector))
 };
 
 // This CTA's share of a distributed level.
@@ -83,6 +87,8 @@ template <class A> struct ClLev {
 template <class A> struct ClL {
     int n0, n1, nr, a, ld, xs, cs;
     unsigned magic;
+    int vec;                  // sweeps and residual by 16-byte vectors of points (cl_step_v)
+    unsigned magicv;
     A* X;                     // buffer 0 at (row -1, column -1); buffer k at X + k*xs; (lr, c) at (lr+1)*ld + c+1
     const A* S;               // stored stencil (component stride cs = maxr*n0); nullptr: FD level 0
     const A* W;               // omega / a_PP (index lr*n0 + c); nullptr: the scalar w0
@@ -94,7 +100,9 @@ template <class A> struct ClL {
     const A* fy;
     __device__ __forceinline__ A* pu(int k) const { return k == 0 ? pu0 : (k == 1 ? pu1 : pu2); }
     __device__ __forceinline__ A* pd(int k) const { return k == 0 ? pd0 : (k == 1 ? pd1 : pd2); }
-    __device__ __forceinline__ A* el(int k, int lr, int col) const { return X + k * xs + (lr + 1) * ld + col + 1; }
+    __device__ __forceinline__ A* el(int k, int lr, int col) const {
+        return X + k * xs + (lr + 1) * ld + col + kClPad;
+    }
     // store v at (lr, c) of buffer k and mirror the CTA's first / last row into the neighbours' ghost rows
     __device__ __forceinline__ void put(int k, int lr, int col, A v) const {
         *el(k, lr, col) = v;
@@ -156,10 +164,12 @@ __device__ __forceinline__ ClL<typename PT<SI>::A> cl_level(const ClShared<SI>& 
     ClL<A> v;
     v.n0 = t.g[l].n0;
     v.n1 = t.g[l].n1;
-    v.ld = v.n0 + 2;
+    v.ld = v.n0 + 2 * kClPad;
     v.xs = (t.maxr[l] + 2) * v.ld;
     v.cs = t.maxr[l] * v.n0;
     v.magic = t.magic[l];
+    v.vec = t.vec[l];
+    v.magicv = t.magicv[l];
     const bool dist = l < t.T;
     v.a = dist ? S.lv[l].a : 0;
     v.nr = dist ? S.lv[l].nr : v.n1;
@@ -257,6 +267,136 @@ __device__ __forceinline__ void cl_residual(const ClL<A>& vin, int kin, int tid,
         const A* xm = v.el(kin, lr, c);
         v.put(1 - kin, lr, c, *v.el(2, lr, c) - cl_apply(v, p, lr, c, xm));
     }
+}
+
+// The points of a CTA's rows as 16-byte vectors (4 FP32 or 2 FP64 consecutive points of a row, rows
+// 16-byte aligned by kClPad): one vector load per neighbouring row, scalar loads of the two points
+// beside the vector, one vector store.  MODE 0: damped Jacobi into buffer 1 - kin; MODE 1: the same
+// from x = 0 (w b); MODE 2: the residual b - A x into buffer 1 - kin.  Per point the operations of
+// cl_sweep / cl_residual / cl_apply in the same order: the same values.  Levels planned with
+// `vec`: n0 a multiple of the vector width, and a 9-point stored stencil or the FD level with
+// kappa = 1.
+template <class A> struct ClVec;
+template <> struct ClVec<float> {
+    using T = float4;
+    static constexpr int n = 4;
+};
+template <> struct ClVec<double> {
+    using T = double2;
+    static constexpr int n = 2;
+};
+
+template <class A>
+__device__ __forceinline__ void cl_vload(const A* p, A* out) {
+    using VT = typename ClVec<A>::T;
+    const VT v = *reinterpret_cast<const VT*>(p);
+    const A* q = reinterpret_cast<const A*>(&v);
+#pragma unroll
+    for (int t = 0; t < ClVec<A>::n; ++t) out[t] = q[t];
+}
+
+template <class A>
+__device__ __forceinline__ void cl_vstore(A* p, const A* in) {
+    using VT = typename ClVec<A>::T;
+    VT v;
+    A* q = reinterpret_cast<A*>(&v);
+#pragma unroll
+    for (int t = 0; t < ClVec<A>::n; ++t) q[t] = in[t];
+    *reinterpret_cast<VT*>(p) = v;
+}
+
+template <int MODE, class A>
+__device__ __forceinline__ void cl_step_v(const ClL<A>& vin, int kin, int tid, int nthr) {
+    constexpr int VN = ClVec<A>::n;
+    const int nv = vin.n0 / VN;
+    if (tid >= vin.nr * nv) return;
+    const ClL<A> v = vin;
+    const int np = v.nr * nv, ld = v.ld, kout = 1 - kin;
+    for (int q = tid; q < np; q += nthr) {
+        const int lr = cl_div(q, v.magicv);
+        const int c = (q - lr * nv) * VN;
+        const int p = lr * v.n0 + c;
+        A b[VN], w[VN], out[VN];
+        cl_vload(v.el(2, lr, c), b);
+        if (MODE != 2) {
+            if (v.W) {
+                cl_vload(v.W + p, w);
+            } else {
+#pragma unroll
+                for (int t = 0; t < VN; ++t) w[t] = v.w0;
+            }
+        }
+        if (MODE == 1) {
+#pragma unroll
+            for (int t = 0; t < VN; ++t) out[t] = w[t] * b[t];
+        } else {
+            const A* xm = v.el(kin, lr, c);
+            A xc[VN], xs[VN], xn[VN];
+            cl_vload(xm, xc);
+            cl_vload(xm - ld, xs);
+            cl_vload(xm + ld, xn);
+            const A xl = xm[-1], xr = xm[VN];
+            A Au[VN];
+            if (v.S == nullptr) {
+#pragma unroll
+                for (int t = 0; t < VN; ++t) {
+                    const A uP = xc[t], uW = t == 0 ? xl : xc[t - 1], uE = t == VN - 1 ? xr : xc[t + 1];
+                    const A K = v.hx2 * (A(2) * uP - uW - uE) + v.hy2 * (A(2) * uP - xs[t] - xn[t]);
+                    Au[t] = v.sigma * uP + v.c * K;
+                }
+            } else {
+                const A sl = xm[-ld - 1], sr = xm[-ld + VN], nl = xm[ld - 1], nrt = xm[ld + VN];
+                A S[9][VN];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) cl_vload(v.S + (long long)k * v.cs + p, S[k]);
+#pragma unroll
+                for (int t = 0; t < VN; ++t) {
+                    const A sW = t == 0 ? sl : xs[t - 1], sE = t == VN - 1 ? sr : xs[t + 1];
+                    const A uW = t == 0 ? xl : xc[t - 1], uE = t == VN - 1 ? xr : xc[t + 1];
+                    const A nW = t == 0 ? nl : xn[t - 1], nE = t == VN - 1 ? nrt : xn[t + 1];
+                    A acc = A(0);
+                    acc += S[0][t] * sW;
+                    acc += S[1][t] * xs[t];
+                    acc += S[2][t] * sE;
+                    acc += S[3][t] * uW;
+                    acc += S[4][t] * xc[t];
+                    acc += S[5][t] * uE;
+                    acc += S[6][t] * nW;
+                    acc += S[7][t] * xn[t];
+                    acc += S[8][t] * nE;
+                    Au[t] = acc;
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < VN; ++t) out[t] = MODE == 0 ? xc[t] + w[t] * (b[t] - Au[t]) : b[t] - Au[t];
+        }
+        cl_vstore(v.el(kout, lr, c), out);
+        if (lr == 0) {
+            A* u = v.pu(kout);
+            if (u) cl_vstore(u + c, out);
+        }
+        if (lr == v.nr - 1) {
+            A* d = v.pd(kout);
+            if (d) cl_vstore(d + c, out);
+        }
+    }
+}
+
+// Sweep or residual of one level: vectors where planned, else point by point.
+template <class A>
+__device__ __forceinline__ void cl_sweep_any(const ClL<A>& v, int kin, bool zero, int tid, int nthr) {
+    if (v.vec) {
+        if (zero) cl_step_v<1>(v, kin, tid, nthr);
+        else cl_step_v<0>(v, kin, tid, nthr);
+    } else {
+        cl_sweep(v, kin, zero, tid, nthr);
+    }
+}
+
+template <class A>
+__device__ __forceinline__ void cl_residual_any(const ClL<A>& v, int kin, int tid, int nthr) {
+    if (v.vec) cl_step_v<2>(v, kin, tid, nthr);
+    else cl_residual(v, kin, tid, nthr);
 }
 
 // b_c = P^T r (r = buffer kr of the fine level f) on the coarse rows this CTA computes.
@@ -383,7 +523,7 @@ __device__ __forceinline__ void cl_stage_async(const ClCtx<SI>& t, int rank, int
                                                int item, int tid, int nthr) {
     const Geo& g = t.g[0];
     const int a = t.rlo[0][rank], nr = t.rlo[0][rank + 1] - a;
-    const int ld0 = g.n0 + 2, xs0 = (t.maxr[0] + 2) * ld0;
+    const int ld0 = g.n0 + 2 * kClPad, xs0 = (t.maxr[0] + 2) * ld0;
     float* B0 = sm + t.off[0] + 2 * xs0;
     const float* bsrc = reinterpret_cast<const float*>(bv.d) + (long long)item * bv.bs;
     if (nr > 0) {
@@ -391,8 +531,8 @@ __device__ __forceinline__ void cl_stage_async(const ClCtx<SI>& t, int rank, int
         for (int p = tid; p < nb0; p += nthr) {
             const int lr = cl_div(p, t.magic[0]) - 1;
             const int row = a + lr, c = p - (lr + 1) * g.n0;
-            if (row >= 0 && row < g.n1) cp_async4(B0 + (lr + 1) * ld0 + c + 1, bsrc + (long long)row * g.n0 + c);
-            else B0[(lr + 1) * ld0 + c + 1] = 0.f;
+            if (row >= 0 && row < g.n1) cp_async4(B0 + (lr + 1) * ld0 + c + kClPad, bsrc + (long long)row * g.n0 + c);
+            else B0[(lr + 1) * ld0 + c + kClPad] = 0.f;
         }
     }
     const int w = g.n0 + 1;
@@ -480,7 +620,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
     // zero the padding columns and ghost rows of every x / b buffer (interiors are written before
     // they are read; the zeros stand for the Dirichlet boundary)
     for (int l = 0; l < L; ++l) {
-        const int ld = t.g[l].n0 + 2, rows = t.maxr[l] + 2, xs = rows * ld;
+        const int ld = t.g[l].n0 + 2 * kClPad, rows = t.maxr[l] + 2, xs = rows * ld;
         const int nrl = l < T ? t.rlo[l][rank + 1] - t.rlo[l][rank] : t.g[l].n1;   // this CTA's rows
         A* base = sm + t.off[l];
         const int nedge = 2 * ld + 2 * rows;          // ghost rows -1 and nrl, two padding columns
@@ -489,8 +629,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
             int idx;
             if (e < ld) idx = e;                                  // ghost row -1
             else if (e < 2 * ld) idx = (nrl + 1) * ld + e - ld;   // ghost row nrl
-            else if (e < 2 * ld + rows) idx = (e - 2 * ld) * ld;  // column -1
-            else idx = (e - 2 * ld - rows) * ld + ld - 1;         // column n0
+            else if (e < 2 * ld + rows) idx = (e - 2 * ld) * ld + kClPad - 1;          // column -1
+            else idx = (e - 2 * ld - rows) * ld + kClPad + t.g[l].n0;                 // column n0
             base[k * xs + idx] = A(0);
         }
     }
@@ -503,27 +643,27 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
         while (pr >= 0 && t.rlo[l][pr + 1] == t.rlo[l][pr]) --pr;
         int nx = rank + 1;
         while (nx < t.C && t.rlo[l][nx + 1] == t.rlo[l][nx]) ++nx;
-        const int ld = t.g[l].n0 + 2, xs = (t.maxr[l] + 2) * ld;
+        const int ld = t.g[l].n0 + 2 * kClPad, xs = (t.maxr[l] + 2) * ld;
         for (int k = 0; k < 3; ++k) {
             v.pu[k] = nullptr;
             v.pd[k] = nullptr;
             if (v.nr > 0 && v.a > 0 && pr >= 0) {
                 const int cnt = t.rlo[l][pr + 1] - t.rlo[l][pr];     // its ghost row below is row cnt
-                v.pu[k] = cl_map(sm + t.off[l] + k * xs + (cnt + 1) * ld + 1, (unsigned)pr);
+                v.pu[k] = cl_map(sm + t.off[l] + k * xs + (cnt + 1) * ld + kClPad, (unsigned)pr);
             }
             if (v.nr > 0 && v.a + v.nr < t.g[l].n1 && nx < t.C)
-                v.pd[k] = cl_map(sm + t.off[l] + k * xs + 1, (unsigned)nx);     // its ghost row -1
+                v.pd[k] = cl_map(sm + t.off[l] + k * xs + kClPad, (unsigned)nx);     // its ghost row -1
         }
     }
     // row table of level T-1 (the restriction into the coarsest level reads every row of it)
     const A** rowtab = reinterpret_cast<const A**>(sm + t.rowtab_off);
     {
         const int l = T - 1;
-        const int ld = t.g[l].n0 + 2;
+        const int ld = t.g[l].n0 + 2 * kClPad;
         for (int i = tid; i < t.g[l].n1; i += nthr) {
             int r = 0;
             while (r + 1 < t.C && t.rlo[l][r + 1] <= i) ++r;
-            A* q = sm + t.off[l] + (i - t.rlo[l][r] + 1) * ld + 1;
+            A* q = sm + t.off[l] + (i - t.rlo[l][r] + 1) * ld + kClPad;
             rowtab[i] = r == rank ? q : cl_map(q, (unsigned)r);
         }
     }
@@ -544,7 +684,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
             constexpr int U = 4;
             const Geo& g = t.g[0];
             const int a = t.rlo[0][rank], nr = t.rlo[0][rank + 1] - a;
-            const int np0 = nr * g.n0, ld0 = g.n0 + 2, xs0 = (t.maxr[0] + 2) * ld0;
+            const int np0 = nr * g.n0, ld0 = g.n0 + 2 * kClPad, xs0 = (t.maxr[0] + 2) * ld0;
             View<SI> bs = view_of(bv, item, 0, g.n0);
             A* B0 = sm + t.off[0] + 2 * xs0;
             // rows a-1 .. a+nr of b (the ghost rows too: the residual of a zero guess is b)
@@ -562,7 +702,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
                 for (int u = 0; u < U; ++u) {
                     const int p = p0 + u * nthr;
                     const int lr = cl_div(p, t.magic[0]) - 1;
-                    if (p < nb0) B0[(lr + 1) * ld0 + p - (lr + 1) * g.n0 + 1] = v[u];
+                    if (p < nb0) B0[(lr + 1) * ld0 + p - (lr + 1) * g.n0 + kClPad] = v[u];
                 }
             }
             if (t.fine0 && !t.w0_const) {
@@ -659,7 +799,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
             const ClL<A>& f = S.lev[l];
             int k = (cur >> l) & 1u;
             for (int sw = 0; sw < t.nu1; ++sw) {
-                cl_sweep(f, k, zero && sw == 0, tid, nthr);
+                cl_sweep_any(f, k, zero && sw == 0, tid, nthr);
                 k ^= 1;
                 cl_step_sync(dist);
             }
@@ -674,7 +814,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
                 }
                 cl_step_sync(dist);                       // b rows were written by this level's restriction
             } else {
-                cl_residual(f, k, tid, nthr);
+                cl_residual_any(f, k, tid, nthr);
                 kr = k ^ 1;
                 cl_step_sync(dist);
             }
@@ -735,7 +875,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
                 cl_prolong_ext(f, cv, k, kc, k, tid, nthr);
                 __syncthreads();
                 for (int sw = 0; sw < t.nu2; ++sw) {
-                    cl_sweep(f, k, false, tid, nthr);
+                    cl_sweep_any(f, k, false, tid, nthr);
                     k ^= 1;
                     cl_step_sync(dist);
                 }

@@ -523,6 +523,12 @@ class Precond : public PrecondBase {
             const Geo& gl = lev[l].g;
             t.g[l] = gl;
             t.magic[l] = (unsigned)((4294967296ULL + (unsigned long long)gl.n0 - 1) / (unsigned long long)gl.n0);
+            // 16-byte vectors of points: the FD level 0 with kappa = 1 and every stored-stencil level
+            constexpr int VN = (int)(16 / sizeof(A));
+            const bool stencil_level = l >= 1 || !fine0;
+            t.vec[l] = (l < L - 1 && gl.n0 % VN == 0 && (stencil_level || !faces)) ? 1 : 0;
+            const unsigned long long nv = (unsigned long long)(gl.n0 / VN > 0 ? gl.n0 / VN : 1);
+            t.magicv[l] = (unsigned)((4294967296ULL + nv - 1) / nv);
             if (l < T) {
                 for (int r = 0; r <= C; ++r)
                     t.rlo[l][r] = l == 0 ? (int)((long long)r * gl.n1 / C) : t.rlo[l - 1][r] / 2;
@@ -535,7 +541,7 @@ class Precond : public PrecondBase {
             } else {
                 t.maxr[l] = gl.n1;
             }
-            t.off[l] = take(3LL * (t.maxr[l] + 2) * (gl.n0 + 2));
+            t.off[l] = take(3LL * (t.maxr[l] + 2) * (gl.n0 + 2 * kClPad));
         }
         if (!nonempty) return false;
         for (int l = 0; l < L; ++l) {

@@ -92,4 +92,6 @@ def test_schedule_autotuner_returns_a_timed_candidate():
     dev()
     best, times = tune_mgrit((48, 40), 1.0, 16, tableau=radau_iia(2), prec_P="fp32", inner_maxit=3, inner_tol=1e-3)
     assert set(times) == {0, 4, 8} and best in times and all(t > 0 for t in times.values())
-    assert times[best] == min(times.values())
+    fastest = min(times, key=times.get)
+    # the fastest MGRIT candidate, unless it beats the substitution by 10% or less
+    assert best == (fastest if fastest == 0 or times[fastest] <= 0.9 * times[0] else 0)
