@@ -15,7 +15,10 @@ Theta_tilde^{-1} (e (x) K z)).  Phi may be nonlinear (inner GMRES with a toleran
 method is used in its residual-correction form all the same.
 
 Reading (the paper is silent):
-* two levels; coarsening factor m dividing nt; C-points n = 0, m, 2m, ..., nt; F-points the rest;
+* two levels; coarsening factor m (2 <= m <= nt); C-points the multiples of m up to nt, F-points the
+  rest; where m does not divide nt the steps after the last C-point form a shorter final interval,
+  relaxed from that C-point, and the coarse recurrence has nt // m steps (the convention of MGRIT
+  codes, XBraid's among them: the coarse grid is every m-th fine point);
 * initial guess u_0 = w_0 (exact) and u_n = 0 for n > 0;
 * one iteration = relaxation ("F": F-relaxation; "FCF": F-, C-, F-relaxation), then the C-point
   residuals r_j = w_{jm} + Phi(u_{jm-1}) - u_{jm}, then the coarse error recurrence
@@ -29,7 +32,7 @@ itself solved by one V-cycle, down to a level solved by substitution.
 
 Parity: pinned (tests) by the exactness property of MGRIT -- after k iterations the first
 (2k+1)m points (FCF) or (k+1)m points (F) equal sequential substitution, for any Phi_c with
-Phi_c(0) = 0 -- by one-iteration convergence with the ideal coarse propagator Phi_c = Phi^m for a
+Phi_c(0) = 0, whether or not m divides nt -- by one-iteration convergence with the ideal coarse propagator Phi_c = Phi^m for a
 linear Phi (two levels) and Phi^m, Phi^(m^2) (three levels), by the coarse S_tilde step on sine
 eigenmodes against the RK stability function R(-m tau lambda), and by the multilevel cycle with
 two levels being the two-level method bit for bit.
@@ -59,8 +62,8 @@ def two_level(phi, phi_c, w, m: int, iters: int = 1, relax: str = "FCF", u=None)
     MGRIT iterations.  w has shape (nt + 1, n); returns u of the same shape."""
     w = np.asarray(w, dtype=np.float64)
     nt = w.shape[0] - 1
-    if m < 1 or nt % m != 0:
-        raise ValueError("the coarsening factor must divide the number of time steps")
+    if m < 1 or m > max(nt, 1):
+        raise ValueError("the coarsening factor must lie in 1 .. nt")
     if relax not in ("F", "FCF"):
         raise ValueError("relaxation is 'F' or 'FCF'")
     if u is None:
@@ -68,7 +71,7 @@ def two_level(phi, phi_c, w, m: int, iters: int = 1, relax: str = "FCF", u=None)
         u[0] = w[0]
     else:
         u = np.array(u, dtype=np.float64)
-    nc = nt // m
+    nc = nt // m               # C-points m, 2m, .., nc m; the steps after nc m are F-points
     for _ in range(iters):
         f_relax(phi, u, w, m)
         if relax == "FCF":

@@ -148,7 +148,11 @@ class Preconditioner:
         self.coarse = None
         self.coarser = []          # levels 1 .. mgrit_levels-1: steps of size m^k tau
         if schur == "mgrit":
-            if self.mgrit_levels < 2 or self.mgrit_m < 1 or self.nt % self.mgrit_m ** (self.mgrit_levels - 1) != 0:
+            if self.mgrit_levels < 2 or self.mgrit_m < 1 or self.mgrit_m > self.nt:
+                raise ValueError("the MGRIT coarsening factor m must lie in 1 .. nt")
+            # two levels take any m (a shorter final interval when m does not divide nt); the
+            # multilevel cycle needs m^(levels-1) to divide nt
+            if self.mgrit_levels > 2 and self.nt % self.mgrit_m ** (self.mgrit_levels - 1) != 0:
                 raise ValueError("the MGRIT coarsening factor m (to the power levels-1) must divide nt")
             for k in range(1, self.mgrit_levels):
                 mk = self.mgrit_m ** k

@@ -25,10 +25,11 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("m,k,relax", [(4, 1, "F"), (4, 1, "FCF"), (3, 2, "F"), (3, 2, "FCF"), (2, 1, "FCF"),
-                                       (6, 1, "FCF")])
+                                       (6, 1, "FCF"), (5, 1, "F"), (5, 2, "FCF"), (7, 2, "F"), (10, 1, "F")])
 def test_mgrit_exact_prefix(m, k, relax):
     """After k iterations the first (k+1)m (F) or (2k+1)m (FCF) points equal sequential
-    substitution, whatever the coarse propagator; the next C-point does not."""
+    substitution, whatever the coarse propagator; the next C-point does not.  m = 5, 7, 10 do not
+    divide nt = 24: the steps after the last C-point form a shorter final interval."""
     nt = 24
     op, P = _precond(nt, m)
     w = np.stack([synth.random_vector(op.nx, 100 + n) for n in range(nt + 1)])
@@ -40,10 +41,11 @@ def test_mgrit_exact_prefix(m, k, relax):
         assert np.abs(u[p] - ref[p]).max() > 1e-10 * np.abs(ref[p]).max()
 
 
-@pytest.mark.parametrize("relax", ["F", "FCF"])
-def test_mgrit_ideal_coarse_propagator_converges_in_one_iteration(relax):
-    """For a linear step Phi (exact stage solves) and Phi_c = Phi^m, one iteration is exact."""
-    nt, m = 24, 4
+@pytest.mark.parametrize("relax,m", [("F", 4), ("FCF", 4), ("F", 5), ("FCF", 7)])
+def test_mgrit_ideal_coarse_propagator_converges_in_one_iteration(relax, m):
+    """For a linear step Phi (exact stage solves) and Phi_c = Phi^m, one iteration is exact (for
+    m = 5, 7 the shorter final interval included)."""
+    nt = 24
     op, P = _precond(nt, m, exact=True)
 
     def phi_m(e):
@@ -110,12 +112,16 @@ def test_mgrit_preconditioned_solve_reaches_the_solution():
 def test_mgrit_rejects_bad_parameters():
     w = np.zeros((9, 4))
     with pytest.raises(ValueError):
-        mgrit.two_level(lambda z: z, lambda z: z, w, 3, 1)          # 3 does not divide 8
+        mgrit.two_level(lambda z: z, lambda z: z, w, 9, 1)          # m beyond the 8 steps
+    with pytest.raises(ValueError):
+        mgrit.two_level(lambda z: z, lambda z: z, w, 0, 1)
     with pytest.raises(ValueError):
         mgrit.two_level(lambda z: z, lambda z: z, w, 2, 1, "C")
     op = build(NS, 1.0, 6, "radau", 2)
     with pytest.raises(ValueError):
-        Preconditioner(op, NS, schur="mgrit", mgrit_m=4)
+        Preconditioner(op, NS, schur="mgrit", mgrit_m=7)
+    with pytest.raises(ValueError):                                 # three levels: 2^2 does not divide 6
+        Preconditioner(op, NS, schur="mgrit", mgrit_m=2, mgrit_levels=3)
 
 
 @pytest.mark.parametrize("relax,iters", [("FCF", 1), ("F", 2)])
