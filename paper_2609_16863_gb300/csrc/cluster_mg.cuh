@@ -509,6 +509,94 @@ __device__ __forceinline__ void cl_prolong_ext(const ClL<A>& fin, const ClL<A>& 
     }
 }
 
+// cl_prolong_ext with 16-byte vectors of fine points (fine n0 a multiple of the vector width): one
+// vector load and store of x_f, the three coarse values beside each vector from each coarse row;
+// per point the operations of cl_prolong_ext in the same order.
+template <class A>
+__device__ __forceinline__ void cl_prolong_ext_v(const ClL<A>& fin, const ClL<A>& cvin, int kx, int kc, int kout,
+                                                 int tid, int nthr) {
+    constexpr int VN = ClVec<A>::n;
+    const int nv = fin.n0 / VN;
+    if (fin.nr == 0 || tid >= (fin.nr + 2) * nv) return;
+    const ClL<A> f = fin, cv = cvin;
+    const int np = (f.nr + 2) * nv;
+    for (int q = tid; q < np; q += nthr) {
+        const int lr = cl_div(q, f.magicv) - 1;
+        const int c = (q - (lr + 1) * nv) * VN;
+        const int F = f.a + lr;
+        if (F < 0 || F >= f.n1) continue;
+        int y0, y1;
+        bool yi;
+        cl_interp(F, y0, y1, yi);
+        const A wy = yi ? A(1) : A(0.5);
+        const A* r0 = cv.el(kc, y0 - cv.a, 0);
+        const A* r1 = cv.el(kc, y1 - cv.a, 0);
+        A xv[VN], out[VN];
+        cl_vload(f.el(kx, lr, c), xv);
+#pragma unroll
+        for (int t = 0; t < VN; ++t) {
+            int x0, x1;
+            bool xi;
+            cl_interp(c + t, x0, x1, xi);
+            const A wx = xi ? A(1) : A(0.5);
+            const A w00 = wy * wx, w01 = xi ? A(0) : w00, w10 = yi ? A(0) : w00, w11 = (xi || yi) ? A(0) : w00;
+            A acc = xv[t];
+            acc += w00 * r0[x0];
+            acc += w01 * r0[x1];
+            acc += w10 * r1[x0];
+            acc += w11 * r1[x1];
+            out[t] = acc;
+        }
+        cl_vstore(f.el(kout, lr, c), out);
+    }
+}
+
+// cl_restrict from a distributed fine level into a distributed coarse one with 16-byte vectors of
+// coarse points: each fine row contributes two vector loads and one scalar; per point the operations
+// of cl_restrict in the same order.  Both levels' n0 must be multiples of the vector width (the fine
+// rows are read as vectors: with an odd fine n0 the row stride n0 + 2 kClPad is odd).
+template <class A>
+__device__ __forceinline__ void cl_restrict_v(const ClL<A>& fin, const ClL<A>& cvin, int kr, int tid, int nthr) {
+    constexpr int VN = ClVec<A>::n;
+    const int nv = cvin.n0 / VN;
+    if (tid >= cvin.nr * nv) return;
+    const ClL<A> f = fin, cv = cvin;
+    const int np = cv.nr * nv;
+    for (int q = tid; q < np; q += nthr) {
+        const int lr = cl_div(q, cv.magicv);
+        const int I0 = (q - lr * nv) * VN;
+        const int J = cv.a + lr;
+        A acc[VN];
+#pragma unroll
+        for (int t = 0; t < VN; ++t) acc[t] = A(0);
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int fj = 2 * J + 1 + dy;
+            const A wy = dy == 0 ? A(1) : A(0.5);
+            const A* row = f.el(kr, fj - f.a, 0) + 2 * I0;     // own or ghost row (zero beyond the boundary)
+            A fv[2 * VN + 1];
+            cl_vload(row, fv);
+            cl_vload(row + VN, fv + VN);
+            fv[2 * VN] = row[2 * VN];                          // the zero column when 2 (I0 + VN) == n0
+#pragma unroll
+            for (int t = 0; t < VN; ++t) {
+                acc[t] += A(0.5) * wy * fv[2 * t];
+                acc[t] += A(1) * wy * fv[2 * t + 1];
+                acc[t] += A(0.5) * wy * fv[2 * t + 2];
+            }
+        }
+        cl_vstore(cv.el(2, lr, I0), acc);
+        if (lr == 0) {
+            A* u = cv.pu(2);
+            if (u) cl_vstore(u + I0, acc);
+        }
+        if (lr == cv.nr - 1) {
+            A* d = cv.pd(2);
+            if (d) cl_vstore(d + I0, acc);
+        }
+    }
+}
+
 // Asynchronous copy of 4 bytes global -> shared (no register round trip).
 __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -820,7 +908,9 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
             }
             cur = (cur & ~(1u << l)) | ((unsigned)k << l);
             const ClL<A>& cv = S.lev[l + 1];
-            cl_restrict(f, cv, kr, dist && l + 1 >= T, rowtab, tid, nthr);
+            // vector restriction: coarse points in vectors and the fine rows 16-byte aligned too
+            if (dist && l + 1 < T && cv.vec && f.n0 % ClVec<A>::n == 0) cl_restrict_v(f, cv, kr, tid, nthr);
+            else cl_restrict(f, cv, kr, dist && l + 1 >= T, rowtab, tid, nthr);
             __syncthreads();
             zero = true;
         }
@@ -872,7 +962,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
                 // x += P x_c in place on own and ghost rows (no remote store: every CTA computes its
                 // ghost rows itself), then the first sweep into the other buffer; a neighbour's
                 // stores of that sweep land in a buffer nobody reads during this step
-                cl_prolong_ext(f, cv, k, kc, k, tid, nthr);
+                if (f.vec) cl_prolong_ext_v(f, cv, k, kc, k, tid, nthr);
+                else cl_prolong_ext(f, cv, k, kc, k, tid, nthr);
                 __syncthreads();
                 for (int sw = 0; sw < t.nu2; ++sw) {
                     cl_sweep_any(f, k, false, tid, nthr);

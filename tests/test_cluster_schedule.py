@@ -354,3 +354,71 @@ def test_cluster_schedule_needs_nonempty_ranges():
     ref = H.solve(b, 1)
     assert not races
     assert np.abs(x - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# alignment of the cluster kernel's 16-byte vector accesses (csrc/cluster_mg.cuh), restated from
+# its address formulas: rows padded by PAD columns on each side, level l's three buffers at an
+# offset that is a multiple of 4 elements, row stride n0 + 2 PAD; a vector of VN = 16 / element
+# bytes points is read or written at element offsets that must be multiples of VN.
+
+PAD = 4
+
+
+def _vector_offsets(sizes, C, VN, faces=False, q1=False):
+    """Element offsets (relative to 16-byte aligned bases) of every vector access one V-cycle
+    makes on CTA 0..C-1, for the dispatch rules of the kernel."""
+    L = len(sizes)
+    T = L - 1
+    rlo = partition(sizes, C)
+    maxr = [max(max(rlo[l][r + 1] - rlo[l][r] for r in range(C)), 1) if l < T else sizes[l][1] for l in range(L)]
+    vec = [l < L - 1 and sizes[l][0] % VN == 0 and (l >= 1 or q1 or not faces) for l in range(L)]
+    offs = []
+    for r in range(C):
+        for l in range(L - 1):
+            n0 = sizes[l][0]
+            ld = n0 + 2 * PAD
+            xs = (maxr[l] + 2) * ld
+            a, nr = rlo[l][r], rlo[l][r + 1] - rlo[l][r]
+
+            def el(k, lr, c):
+                return k * xs + (lr + 1) * ld + c + PAD
+
+            if vec[l]:                                   # sweeps and residual
+                for lr in range(nr):
+                    for c in range(0, n0, VN):
+                        p = lr * n0 + c
+                        offs += [el(k, lr, c) for k in range(3)] + [el(0, lr, c) - ld, el(0, lr, c) + ld, p]
+                        offs += [q * maxr[l] * n0 + p for q in range(9)]                 # staged stencil
+                        offs += [q * sizes[l][0] * sizes[l][1] + a * n0 + p for q in range(9)]   # from L2
+                for lr in range(-1, nr + 1):             # interpolation into this level
+                    for c in range(0, n0, VN):
+                        offs.append(el(0, lr, c))
+            cv = l + 1
+            if cv < T and vec[cv] and n0 % VN == 0:      # restriction into the next distributed level
+                n0c = sizes[cv][0]
+                ldc = n0c + 2 * PAD
+                xsc = (maxr[cv] + 2) * ldc
+                for lr in range(rlo[cv][r + 1] - rlo[cv][r]):
+                    J = rlo[cv][r] + lr
+                    for I0 in range(0, n0c, VN):
+                        for dy in (-1, 0, 1):
+                            row = el(0, 2 * J + 1 + dy - a, 0) + 2 * I0
+                            offs += [row, row + VN]
+                        offs.append(2 * xsc + (lr + 1) * ldc + I0 + PAD)
+    return offs
+
+
+@pytest.mark.parametrize("ns", [(256, 256), (129, 97), (97, 33), (130, 70), (48, 40), (64, 64), (33, 17), (120, 17),
+                                (255, 257), (100, 97)])
+@pytest.mark.parametrize("ebytes", [4, 8])
+def test_vector_accesses_are_16_byte_aligned(ns, ebytes):
+    VN = 16 // ebytes
+    for C in (16, 8):
+        sizes, rlo = plan(ns, C)
+        if rlo is None:
+            continue
+        for faces in (False, True):
+            offs = _vector_offsets(sizes, C, VN, faces=faces)
+            bad = [o for o in offs if o % VN]
+            assert not bad, (ns, C, faces, bad[:5])
