@@ -104,7 +104,7 @@ def batched_arm(args):
     for w in ws:
         st = torch.cuda.Stream(device=dev)
         m_req = 8 if args.mgrit_m < 0 else args.mgrit_m
-        m = m_req if m_req > 1 and w.nt % m_req == 0 and w.nt > m_req else 0
+        m = m_req if 1 < m_req and w.nt // m_req >= 2 else 0
         solvers.append(Solver(w.n, w.T, w.nt, tableau=radau_iia(w.s), prec_P=args.prec, inner_maxit=3,
                               inner_tol=1e-3, tol=w.tol, stream=st.cuda_stream, mgrit_m=m))
         fs.append(torch.from_numpy(w.f).to(dev))
@@ -150,7 +150,7 @@ def adjoint_arm(args):
     dev = torch.device("cuda", 0)
     w = synth.workload_adjoint_2d()
     m_req = 8 if args.mgrit_m < 0 else args.mgrit_m
-    mg_m = m_req if w.nt % max(m_req, 1) == 0 else 0
+    mg_m = m_req if 1 < m_req <= w.nt else 0
     cfg = dict(n=w.n, T=w.T, nt=w.nt, tableau=radau_iia(w.s), prec_P=args.prec, tol=1e-9, maxit=200, ckpt_every=8,
                inner_maxit=3, inner_tol=1e-3, mgrit_m=mg_m)
     lo = w.nt * w.nx
@@ -393,7 +393,7 @@ def precond_case(args):
     from paper_2609_16863_gb300 import Solver, radau_iia
     w = synth.workload_fp32_precond_2d(N=256, nt=16, s=3)
     m_req = 8 if args.mgrit_m < 0 else args.mgrit_m
-    m = m_req if w.nt % max(m_req, 1) == 0 and w.nt > m_req else 0
+    m = m_req if 1 < m_req <= w.nt else 0
     S = Solver(w.n, w.T, w.nt, tableau=radau_iia(3), prec_P=args.prec, inner_maxit=3, inner_tol=1e-3, mgrit_m=m)
     g = torch.Generator(device="cuda:0").manual_seed(5)
     r = torch.randn(S.n_st, dtype=torch.float64, device="cuda:0", generator=g)
@@ -564,7 +564,7 @@ def main():
                                  inner_maxit=3, inner_tol=1e-3, restart=1)
         tuned = {str(k): round(v, 3) for k, v in tuned.items()}
     else:
-        mg_m = args.mgrit_m if w.nt % max(args.mgrit_m, 1) == 0 else 0
+        mg_m = args.mgrit_m if 1 < args.mgrit_m <= w.nt else 0
     S = Solver(w.n, w.T, w.nt, prec_P=args.prec, inner_maxit=3, inner_tol=1e-3, mgrit_m=mg_m, **common)
     f = torch.from_numpy(w.f).to(dev)
     u0 = torch.from_numpy(w.u0).to(dev)

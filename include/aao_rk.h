@@ -107,10 +107,12 @@ typedef struct {
                           * states, one aao_rk_grad_kappa(accumulate = 1) call per window */
     void* stream;        /* cudaStream_t for every call on the handle; NULL = default stream */
     int mgrit_m;         /* S_tilde's time recurrence: 0 = forward substitution (Eq. AppSchur);
-                          * m >= 2 (m divides nt) = one two-level MGRIT iteration with coarsening
-                          * factor m and F-relaxation, the coarse step being the same substitution
-                          * step with step size m tau (the parallel implementation of Sec. 5);
-                          * P_tilde^T runs it on the backward recurrence in reversed time */
+                          * 2 <= m <= nt = one two-level MGRIT iteration with coarsening factor m
+                          * and F-relaxation, the coarse step being the same substitution step with
+                          * step size m tau (the parallel implementation of Sec. 5).  C-points are
+                          * the multiples of m; where m does not divide nt the steps after the last
+                          * C-point form a shorter final interval relaxed from it.  P_tilde^T runs
+                          * it on the backward recurrence in reversed time */
     int precond_side;    /* 0: right preconditioning, FGMRES with P_R = P_tilde (Algorithm 1 with
                           * P_L = I; the sequential runs of Sec. 5.1); 1: left preconditioning,
                           * P_L = P_tilde and P_R = I (Algorithm 1; the parallel runs of Sec. 5.2),

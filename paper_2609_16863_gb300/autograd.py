@@ -29,7 +29,7 @@ def _window_solver(cache, cfg, kappa, nt_w):
         # raises), so it may take more outer iterations than the forward solve's cap
         c["maxit"] = max(cfg.get("maxit", 100), 200)
         m = int(c.get("mgrit_m", 0) or 0)
-        c["mgrit_m"] = m if m > 1 and nt_w % m == 0 and nt_w > m else 0    # MGRIT only where it divides
+        c["mgrit_m"] = m if 1 < m < nt_w else 0    # MGRIT only where a window has two or more intervals
         cache[nt_w] = Solver(kappa=kappa, **c)
     return cache[nt_w]
 

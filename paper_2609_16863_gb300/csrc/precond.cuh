@@ -90,14 +90,16 @@ class Precond : public PrecondBase {
     cudaStream_t cur_stream = nullptr;     // stream of the next launch (capture stream while capturing)
     cudaStream_t cap_stream = nullptr;
     // one captured graph per step kind [transpose][kind]: 0 one time step, 1 a batched MGRIT
-    // relaxation step, 2 the batched C-point residual step
-    cudaGraphExec_t gexec[2][3] = {};
-    long long graph_nodes[2][3] = {};
+    // relaxation step, 2 the batched C-point residual step, 3 a batched relaxation step that also
+    // relaxes the shorter final interval (mg_r > 0)
+    cudaGraphExec_t gexec[2][4] = {};
+    long long graph_nodes[2][4] = {};
     StepPtrs* stepp = nullptr;
     // two-level MGRIT for S_tilde's recurrence (mg_m = 0: forward substitution): the coarse
     // propagator is the substitution step of a second preconditioner built for step size
-    // mg_m tau and mg_nc = nt / mg_m steps
-    int mg_m = 0, mg_nc = 0;
+    // mg_m tau and mg_nc = nt / mg_m (rounded down) steps; C-points are the multiples of mg_m, and
+    // the mg_r = nt - mg_nc mg_m steps after the last one form a shorter final interval
+    int mg_m = 0, mg_nc = 0, mg_r = 0;
     std::unique_ptr<Handle> hc;
     Precond* coarse = nullptr;
     double* ebuf = nullptr;        // (nc+1)*nx: coarse error recurrence
@@ -161,7 +163,7 @@ class Precond : public PrecondBase {
         if (ev_start) cudaEventDestroy(ev_start);
         ev_start = nullptr;
         for (int i = 0; i < 2; ++i)
-            for (int k = 0; k < 3; ++k) {
+            for (int k = 0; k < 4; ++k) {
                 if (gexec[i][k]) cudaGraphExecDestroy(gexec[i][k]);
                 gexec[i][k] = nullptr;
             }
@@ -356,8 +358,9 @@ class Precond : public PrecondBase {
         if (h->opt.mgrit_m > 0) {
             mg_m = h->opt.mgrit_m;
             mg_nc = h->nt / mg_m;
+            mg_r = h->nt - mg_nc * mg_m;
         }
-        const long long steps_b = mg_nc > 1 ? mg_nc : 1;     // items of a batched step
+        const long long steps_b = std::max(mg_nc + (mg_r > 0 ? 1 : 0), 1);     // items of a batched step
         AAO_TRY(ar.alloc(&wbuf, (size_t)((h->nt + 1) * g0.nx)));
         AAO_TRY(ar.alloc(&tbuf, (size_t)(steps_b * item)));
         AAO_TRY(ar.alloc(&qbuf, (size_t)(steps_b * item)));
@@ -1014,12 +1017,12 @@ class Precond : public PrecondBase {
         return AAO_OK;
     }
 
-    // A batched step of the recurrence over MGRIT's mg_nc intervals (items b = 0..nc-1 at time
+    // A batched step of the recurrence over B of MGRIT's intervals (items b = 0..B-1 at time
     // indices sp->n +- b mg_m), or with `residual` the C-point residuals into the coarse source.
-    aao_status schur_step_b(int transpose, int residual) {
+    aao_status schur_step_b(int transpose, int residual, int B) {
         const Geo& g = h->g;
         const int s = h->s;
-        const int B = mg_nc, stride = mg_m;
+        const int stride = mg_m;
         const long long item = (long long)s * g.nx;
         const unsigned nbr = blocks_for_rows(g.R);
         if (!transpose) {
@@ -1047,7 +1050,8 @@ class Precond : public PrecondBase {
     }
 
     aao_status step_of_kind(int transpose, int kind) {
-        return kind == 0 ? schur_step(transpose) : schur_step_b(transpose, kind == 2);
+        if (kind == 0) return schur_step(transpose);
+        return schur_step_b(transpose, kind == 2, kind == 3 ? mg_nc + 1 : mg_nc);
     }
 
     // Capture one step of a kind into a CUDA graph (on a private stream) the first time
@@ -1154,6 +1158,12 @@ class Precond : public PrecondBase {
             launch(k_step_set, 1, 1, 0, W->st(), W->stepp, z, (const double*)nullptr, c * m);
             AAO_TRY(W->run_steps(0, 0, m - 1));
         }
+        if (mg_r > 0) {           // the shorter final interval, from the last C-point
+            Precond* W = work[nc % K];
+            AAO_CUDA_TRY(cudaStreamWaitEvent(W->st(), ev_c[nc], 0));
+            launch(k_step_set, 1, 1, 0, W->st(), W->stepp, z, (const double*)nullptr, nc * m);
+            AAO_TRY(W->run_steps(0, 0, mg_r));
+        }
         for (int w = 0; w < K; ++w) {
             AAO_CUDA_TRY(cudaEventRecord(ev_join[w], wst[w]));
             AAO_CUDA_TRY(cudaStreamWaitEvent(st(), ev_join[w], 0));
@@ -1200,6 +1210,12 @@ class Precond : public PrecondBase {
             launch(k_step_set, 1, 1, 0, W->st(), W->stepp, z, r, nt - c * m - 1);
             AAO_TRY(W->run_steps(1, 0, m - 1));
         }
+        if (mg_r > 0) {           // the shorter final interval (the first steps in time)
+            Precond* W = work[nc % K];
+            AAO_CUDA_TRY(cudaStreamWaitEvent(W->st(), ev_c[nc], 0));
+            launch(k_step_set, 1, 1, 0, W->st(), W->stepp, z, r, nt - nc * m - 1);
+            AAO_TRY(W->run_steps(1, 0, mg_r));
+        }
         for (int w = 0; w < K; ++w) {
             AAO_CUDA_TRY(cudaEventRecord(ev_join[w], wst[w]));
             AAO_CUDA_TRY(cudaStreamWaitEvent(st(), ev_join[w], 0));
@@ -1232,7 +1248,10 @@ class Precond : public PrecondBase {
         launch(k_mgrit_cpoints, nb, 256, 0, st(), z, (const double*)ebuf, nx, nc, m, 0, 1, 0, 1);
         launch(k_step_set, 1, 1, 0, st(), stepp, z, (const double*)nullptr, 0);
         AAO_LAUNCH_CHECK();
-        return run_steps(0, 1, m - 1);
+        // the final F-relaxation; its first mg_r steps also relax the shorter final interval from
+        // the last C-point
+        if (mg_r > 0) AAO_TRY(run_steps(0, 3, mg_r));
+        return run_steps(0, 1, m - 1 - mg_r);
     }
 
     // The same for S_tilde^T's backward recurrence u_nt = r_{v,nt}, u_n = Phi^T(u_{n+1}) + r_{v,n},
@@ -1255,7 +1274,8 @@ class Precond : public PrecondBase {
         launch(k_mgrit_cpoints, nb, 256, 0, st(), z, (const double*)ebuf, nx, nc, m, nt, -1, nc, -1);
         launch(k_step_set, 1, 1, 0, st(), stepp, z, r, nt - 1);
         AAO_LAUNCH_CHECK();
-        return run_steps(1, 1, m - 1);
+        if (mg_r > 0) AAO_TRY(run_steps(1, 3, mg_r));
+        return run_steps(1, 1, m - 1 - mg_r);
     }
 
     aao_status mgrit_forward(double* z) { return nwork ? mgrit_dataflow_forward(z) : mgrit_batched_forward(z); }

@@ -286,8 +286,8 @@ static aao_status validate(const aao_grid* grid, double tau, int nt, const aao_t
         set_error("precond_side must be 0 (right) or 1 (left)");
         return AAO_ERR_ARG;
     }
-    if (o->mgrit_m < 0 || o->mgrit_m == 1 || (o->mgrit_m > 0 && nt % o->mgrit_m != 0)) {
-        set_error("mgrit_m must be 0 (substitution) or a divisor m >= 2 of nt");
+    if (o->mgrit_m < 0 || o->mgrit_m == 1 || o->mgrit_m > nt) {
+        set_error("mgrit_m must be 0 (substitution) or an m with 2 <= m <= nt");
         return AAO_ERR_ARG;
     }
     if (o->ckpt_every != 0) {

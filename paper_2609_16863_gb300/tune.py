@@ -19,9 +19,10 @@ from typing import Dict, Iterable, Optional, Sequence, Tuple
 from .api import Solver
 
 
-def mgrit_candidates(nt: int, factors: Iterable[int] = (4, 8, 16, 32)) -> list:
-    """0 (substitution) and every factor m that divides nt with at least two intervals."""
-    return [0] + [m for m in factors if nt % m == 0 and nt // m >= 2]
+def mgrit_candidates(nt: int, factors: Iterable[int] = (4, 6, 8, 10, 12, 16, 32)) -> list:
+    """0 (substitution) and every factor m with at least two C-point intervals (m need not divide
+    nt: the steps after the last C-point form a shorter final interval)."""
+    return [0] + [m for m in factors if nt // m >= 2]
 
 
 def tune_mgrit(n: Sequence[int], T: float, nt: int, candidates: Optional[Iterable[int]] = None,

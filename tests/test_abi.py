@@ -146,7 +146,7 @@ SETUP_BAD = [
     ("opts.mg_pre", -1, b"mg_pre"), ("opts.mg_post", -1, b"mg_pre"), ("opts.mg_omega", 0.0, b"mg_omega"),
     ("opts.prec_P", 7, b"precision"), ("fp64_fp32", None, b"FP64"), ("bf16_fp32", None, b"16-bit"),
     ("fp16_bf16", None, b"16-bit"), ("null_grid", None, b"null"), ("null_out", None, b"null output"),
-    ("opts.mgrit_m", 1, b"mgrit_m"), ("opts.mgrit_m", 3, b"mgrit_m"), ("opts.mgrit_m", -2, b"mgrit_m"),
+    ("opts.mgrit_m", 1, b"mgrit_m"), ("opts.mgrit_m", 5, b"mgrit_m"), ("opts.mgrit_m", -2, b"mgrit_m"),
     ("opts.precond_side", 2, b"precond_side"),
     ("opts.relax_matvec", -1.0, b"relax_matvec"), ("opts.relax_matvec", float("nan"), b"relax_matvec"),
     ("opts.relax_matvec", float("inf"), b"relax_matvec"),
