@@ -603,6 +603,23 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) 
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
 }
 
+// Asynchronous copy of 16 bytes global -> shared (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+// n floats global -> shared: 16-byte copies where both ends are 16-byte aligned and n is a multiple
+// of 4, else 4-byte copies.
+__device__ __forceinline__ void cl_copy_async(float* dst, const float* src, int n, int tid, int nthr) {
+    if (((reinterpret_cast<unsigned long long>(dst) | reinterpret_cast<unsigned long long>(src)) & 15ULL) == 0 &&
+        (n & 3) == 0) {
+        for (int p = tid * 4; p < n; p += nthr * 4) cp_async16(dst + p, src + p);
+    } else {
+        for (int p = tid; p < n; p += nthr) cp_async4(dst + p, src + p);
+    }
+}
+
 // Staging for FP32 storage: every copy (b with ghost rows, faces, this CTA's stencil rows and rows
 // of the coarsest inverse) is issued asynchronously before one wait; the Jacobi weights follow
 // from the staged data.  Same values as the register path.
@@ -614,7 +631,18 @@ __device__ __forceinline__ void cl_stage_async(const ClCtx<SI>& t, int rank, int
     const int ld0 = g.n0 + 2 * kClPad, xs0 = (t.maxr[0] + 2) * ld0;
     float* B0 = sm + t.off[0] + 2 * xs0;
     const float* bsrc = reinterpret_cast<const float*>(bv.d) + (long long)item * bv.bs;
-    if (nr > 0) {
+    const bool b16 = (g.n0 & 3) == 0 && (reinterpret_cast<unsigned long long>(bsrc) & 15ULL) == 0;
+    if (nr > 0 && b16) {
+        // rows of 16-byte vectors (padded shared rows start aligned)
+        const int nv = g.n0 / 4, nb0 = (nr + 2) * nv;
+        for (int q = tid; q < nb0; q += nthr) {
+            const int lr = cl_div(q, t.magicv[0]) - 1;
+            const int row = a + lr, c = (q - (lr + 1) * nv) * 4;
+            float* d = B0 + (lr + 1) * ld0 + c + kClPad;
+            if (row >= 0 && row < g.n1) cp_async16(d, bsrc + (long long)row * g.n0 + c);
+            else *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else if (nr > 0) {
         const int nb0 = (nr + 2) * g.n0;
         for (int p = tid; p < nb0; p += nthr) {
             const int lr = cl_div(p, t.magic[0]) - 1;
@@ -639,14 +667,13 @@ __device__ __forceinline__ void cl_stage_async(const ClCtx<SI>& t, int rank, int
         const int npl = dist ? (t.rlo[l][rank + 1] - al) * gl.n0 : (int)gl.nx;
         const int cs = t.maxr[l] * gl.n0;
         const float* src = reinterpret_cast<const float*>(t.sten[l]) + (long long)al * gl.n0;
-        for (int q = 0; q < 9; ++q)
-            for (int p = tid; p < npl; p += nthr) cp_async4(sm + t.soff[l] + q * cs + p, src + (long long)q * gl.nx + p);
+        for (int q = 0; q < 9; ++q) cl_copy_async(sm + t.soff[l] + q * cs, src + (long long)q * gl.nx, npl, tid, nthr);
     }
     if (!t.dinv_global) {
         const int nc = (int)t.g[L - 1].nx;
         const int n = (t.cs[rank + 1] - t.cs[rank]) * nc;
         const float* src = reinterpret_cast<const float*>(t.Dinv) + (long long)t.cs[rank] * nc;
-        for (int p = tid; p < n; p += nthr) cp_async4(sm + t.dinv_off + p, src + p);
+        cl_copy_async(sm + t.dinv_off, src, n, tid, nthr);
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
