@@ -90,7 +90,9 @@ template <class A> struct ClL {
     int vec;                  // sweeps and residual by 16-byte vectors of points (cl_step_v)
     unsigned magicv;
     A* X;                     // buffer 0 at (row -1, column -1); buffer k at X + k*xs; (lr, c) at (lr+1)*ld + c+1
-    const A* S;               // stored stencil (component stride cs = maxr*n0); nullptr: FD level 0
+    const A* S;               // stored stencil (component stride cs = maxr*n0); nullptr: FD level 0 (or Sg)
+    const void* Sg;           // stencil in global memory in the storage type (16-bit: times Ssc[k]), read by
+    const float* Ssc;         //   the vector steps only; nullptr: S
     const A* W;               // omega / a_PP (index lr*n0 + c); nullptr: the scalar w0
     A w0;
     A *pu0, *pu1, *pu2;       // neighbours' ghost rows (see ClLev)
@@ -174,12 +176,20 @@ __device__ __forceinline__ ClL<typename PT<SI>::A> cl_level(const ClShared<SI>& 
     v.a = dist ? S.lv[l].a : 0;
     v.nr = dist ? S.lv[l].nr : v.n1;
     v.X = sm + t.off[l];
+    v.Sg = nullptr;
+    v.Ssc = nullptr;
     if ((l == 0 && t.fine0) || (t.soff[l] < 0 && !t.sten_global[l])) {
         v.S = nullptr;
     } else if (t.sten_global[l]) {
         // the level's stencil in global memory: component stride n_x, rows from this CTA's first
-        v.S = reinterpret_cast<const A*>(t.sten[l]) + (long long)v.a * v.n0;
         v.cs = (int)t.g[l].nx;
+        if constexpr (std::is_same<SI, A>::value) {
+            v.S = reinterpret_cast<const A*>(t.sten[l]) + (long long)v.a * v.n0;
+        } else {
+            v.S = nullptr;
+            v.Sg = t.sten[l] + (long long)v.a * v.n0;
+            v.Ssc = t.sten_sc[l];
+        }
     } else {
         v.S = sm + t.soff[l];
     }
@@ -305,7 +315,7 @@ __device__ __forceinline__ void cl_vstore(A* p, const A* in) {
     *reinterpret_cast<VT*>(p) = v;
 }
 
-template <int MODE, class A>
+template <int MODE, class SI, class A>
 __device__ __forceinline__ void cl_step_v(const ClL<A>& vin, int kin, int tid, int nthr) {
     constexpr int VN = ClVec<A>::n;
     const int nv = vin.n0 / VN;
@@ -337,7 +347,7 @@ __device__ __forceinline__ void cl_step_v(const ClL<A>& vin, int kin, int tid, i
             cl_vload(xm + ld, xn);
             const A xl = xm[-1], xr = xm[VN];
             A Au[VN];
-            if (v.S == nullptr) {
+            if (v.S == nullptr && v.Sg == nullptr) {
 #pragma unroll
                 for (int t = 0; t < VN; ++t) {
                     const A uP = xc[t], uW = t == 0 ? xl : xc[t - 1], uE = t == VN - 1 ? xr : xc[t + 1];
@@ -347,8 +357,25 @@ __device__ __forceinline__ void cl_step_v(const ClL<A>& vin, int kin, int tid, i
             } else {
                 const A sl = xm[-ld - 1], sr = xm[-ld + VN], nl = xm[ld - 1], nrt = xm[ld + VN];
                 A S[9][VN];
+                if constexpr (!std::is_same<SI, A>::value) {
+                    if (v.Sg) {
+                        // 16-bit storage in global memory: VN values (8 bytes) per component, times its scale
+                        const SI* g = reinterpret_cast<const SI*>(v.Sg) + p;
 #pragma unroll
-                for (int k = 0; k < 9; ++k) cl_vload(v.S + (long long)k * v.cs + p, S[k]);
+                        for (int k = 0; k < 9; ++k) {
+                            const uint2 raw = *reinterpret_cast<const uint2*>(g + (long long)k * v.cs);
+                            const SI* e = reinterpret_cast<const SI*>(&raw);
+#pragma unroll
+                            for (int t = 0; t < VN; ++t) S[k][t] = PT<SI>::ld(e[t]) * v.Ssc[k];
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) cl_vload(v.S + (long long)k * v.cs + p, S[k]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) cl_vload(v.S + (long long)k * v.cs + p, S[k]);
+                }
 #pragma unroll
                 for (int t = 0; t < VN; ++t) {
                     const A sW = t == 0 ? sl : xs[t - 1], sE = t == VN - 1 ? sr : xs[t + 1];
@@ -383,19 +410,19 @@ __device__ __forceinline__ void cl_step_v(const ClL<A>& vin, int kin, int tid, i
 }
 
 // Sweep or residual of one level: vectors where planned, else point by point.
-template <class A>
+template <class SI, class A>
 __device__ __forceinline__ void cl_sweep_any(const ClL<A>& v, int kin, bool zero, int tid, int nthr) {
     if (v.vec) {
-        if (zero) cl_step_v<1>(v, kin, tid, nthr);
-        else cl_step_v<0>(v, kin, tid, nthr);
+        if (zero) cl_step_v<1, SI>(v, kin, tid, nthr);
+        else cl_step_v<0, SI>(v, kin, tid, nthr);
     } else {
         cl_sweep(v, kin, zero, tid, nthr);
     }
 }
 
-template <class A>
+template <class SI, class A>
 __device__ __forceinline__ void cl_residual_any(const ClL<A>& v, int kin, int tid, int nthr) {
-    if (v.vec) cl_step_v<2>(v, kin, tid, nthr);
+    if (v.vec) cl_step_v<2, SI>(v, kin, tid, nthr);
     else cl_residual(v, kin, tid, nthr);
 }
 
@@ -870,9 +897,12 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
                 const int cs = t.maxr[l] * gl.n0;
                 const SI* src = t.sten[l] + (long long)al * gl.n0;
                 if (t.sten_global[l]) {
-                    // read in place (planned only where the storage type is the arithmetic type)
-                    for (int p = tid; p < npl; p += nthr)
-                        sm[t.woff[l] + p] = t.omega / reinterpret_cast<const A*>(src)[4 * gl.nx + p];
+                    // read in place by the vector steps: only the Jacobi weights are staged
+                    for (int p = tid; p < npl; p += nthr) {
+                        A ctr = PT<SI>::ld(src[4 * gl.nx + p]);
+                        if constexpr (PT<SI>::scaled) ctr *= t.sten_sc[l][4];
+                        sm[t.woff[l] + p] = t.omega / ctr;
+                    }
                     continue;
                 }
                 for (int p = tid; p < npl; p += nthr) {
@@ -914,7 +944,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
             const ClL<A>& f = S.lev[l];
             int k = (cur >> l) & 1u;
             for (int sw = 0; sw < t.nu1; ++sw) {
-                cl_sweep_any(f, k, zero && sw == 0, tid, nthr);
+                cl_sweep_any<SI>(f, k, zero && sw == 0, tid, nthr);
                 k ^= 1;
                 cl_step_sync(dist);
             }
@@ -929,7 +959,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
                 }
                 cl_step_sync(dist);                       // b rows were written by this level's restriction
             } else {
-                cl_residual_any(f, k, tid, nthr);
+                cl_residual_any<SI>(f, k, tid, nthr);
                 kr = k ^ 1;
                 cl_step_sync(dist);
             }
@@ -993,7 +1023,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_cluster_mg(const ClCtx<SI>* _
                 else cl_prolong_ext(f, cv, k, kc, k, tid, nthr);
                 __syncthreads();
                 for (int sw = 0; sw < t.nu2; ++sw) {
-                    cl_sweep_any(f, k, false, tid, nthr);
+                    cl_sweep_any<SI>(f, k, false, tid, nthr);
                     k ^= 1;
                     cl_step_sync(dist);
                 }

@@ -494,7 +494,9 @@ class Precond : public PrecondBase {
         const bool faces = fine0 && h->has_kappa;
         const bool same = std::is_same<SI, A>::value;
         const bool w0c = lean >= 1 && fine0 && !faces;
-        if (lean >= 2 && !same) return false;
+        // lean >= 2 reads coarse stencils from global memory: in place where the storage type is the
+        // arithmetic type, else (16-bit storage) through the vector steps only, so those levels
+        // must take vectors (checked below)
         std::memset(&t, 0, sizeof(t));
         t.C = C;
         t.L = L;
@@ -510,7 +512,7 @@ class Precond : public PrecondBase {
         t.fy = facesA.fy;
         t.w0_const = w0c ? 1 : 0;
         t.dinv_global = lean >= 1 ? 1 : 0;
-        for (int l = 1; l < L - 1; ++l) t.sten_global[l] = (lean >= 3 || (lean == 2 && l == 1)) ? 1 : 0;
+
         long long o = 0;
         auto take = [&](long long n) {
             long long at = o;
@@ -547,6 +549,10 @@ class Precond : public PrecondBase {
             t.off[l] = take(3LL * (t.maxr[l] + 2) * (gl.n0 + 2 * kClPad));
         }
         if (!nonempty) return false;
+        for (int l = 1; l < L - 1; ++l) {
+            t.sten_global[l] = (lean >= 3 || (lean == 2 && l == 1)) ? 1 : 0;
+            if (t.sten_global[l] && !same && !t.vec[l]) return false;
+        }
         for (int l = 0; l < L; ++l) {
             t.soff[l] = t.woff[l] = -1;
             if ((l >= 1 || !fine0) && l < L - 1 && !t.sten_global[l]) t.soff[l] = take(9LL * t.maxr[l] * lev[l].g.n0);

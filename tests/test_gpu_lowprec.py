@@ -129,12 +129,14 @@ INNER_BOUND = {"fp32": 2e-5, "fp16": 1e-3, "bf16": 2e-3}
                                                        ((64, 32), 36, "fp16", "fp16", False),
                                                        ((16, 16, 24), 4, "bf16", "bf16", False),
                                                        ((64, 64), 12, "bf16", "bf16", True),
-                                                       ((256, 256), 16, "fp32", "fp32", True)])
+                                                       ((256, 256), 16, "fp32", "fp32", True),
+                                                       ((256, 256), 12, "bf16", "bf16", True)])
 def test_inner_solve_matches_storage_emulation(ns, nb, precP, precI, cluster):
     """Batched inner GMRES (3 fixed iterations) per time block; batches of more than 32 items take
     the level kernels and the on-chip tail instead of one cluster per item, batches of 8 to 32 the
-    8-CTA cluster plan (at 256^2 FP32 the lean one: level-1 stencil and coarsest inverse read from
-    L2, a scalar level-0 Jacobi weight), which gives the same values as the staged layout."""
+    8-CTA cluster plan (at 256^2 the lean one: level-1 stencil and coarsest inverse read from L2 --
+    in BF16 storage converted with their scales by the vector steps -- and a scalar level-0 Jacobi
+    weight), which gives the same values as the staged layout."""
     s = 2
     S, op, P = make(ns, nb, s, precP, precI)
     E = emulation(P, precP, precI, nb, cluster)
