@@ -658,11 +658,15 @@ def main():
                 if tok in name:
                     short = tok
                     break
+            ms = re.search(r"k_strip2d_stI([fd])Li(\d)E", name)
+            if ms:
+                short = (f"k_strip2d_st<{'float' if ms.group(1) == 'f' else 'double'}, "
+                         f"{ {'0': 'smooth', '1': 'smooth_zero', '2': 'residual'}[ms.group(2)] }>")
             mv = re.search(r"k_vec16I(\w+?)Li(\d)E", name)
             if mv:
                 short = (f"k_vec16<{'bf16' if 'bfloat' in mv.group(1) else 'fp16'}, "
                          f"{ {'0': 'smooth', '1': 'smooth_zero', '2': 'residual'}[mv.group(2)] }>")
-            if short.startswith("k_strip2dI"):
+            if short.startswith("k_strip2dI") and not ms:
                 mode = {"0": "smooth", "1": "smooth_zero", "2": "residual"}[short[-1]]
                 short = f"k_strip2d<{'float' if short[10] == 'f' else 'double'}, {mode}>"
             rows.append({"kernel": short, "mangled": name, "launches": int(n), "ms": float(kms), "bytes": float(kby)})
