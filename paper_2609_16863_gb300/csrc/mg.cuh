@@ -478,6 +478,115 @@ __global__ void __launch_bounds__(kStripThreads) k_strip2d(LevelOp<S> op, int B,
     }
 }
 
+// The same streaming form for a 2D level with a stored 9-point stencil (a coarse Galerkin level;
+// unscaled storage): the stencil's 9 component rows are read as 16-byte vectors beside x (the
+// stencil is shared by all items, so it stays in L1/L2), the corner and side neighbours of the
+// vector come from the three rows in registers plus two scalars per row.  Per point the operations
+// of level_apply_k<2> in its order (neighbours beyond the grid read as zero instead of being
+// skipped: the same value) and of k_smooth / k_residual: x + omega (b - A x) / a_PP.
+template <class S, int MODE>
+__global__ void __launch_bounds__(kStripThreads) k_strip2d_st(LevelOp<S> op, int B, const int* active, Vec<S> xin,
+                                                              Vec<S> bv, Vec<S> out, S omega) {
+    pdl_prologue();
+    static_assert(!PT<S>::scaled, "unscaled storage only");
+    using VT = typename Vec16<S>::T;
+    constexpr int V = Vec16<S>::n;
+    const Geo g = op.g;
+    const int b = blockIdx.y;
+    if (b >= B || (active && !active[b])) return;
+    const int n0 = g.n0, n1 = g.n1;
+    const int tpr = n0 / V;
+    const int tx = threadIdx.x % tpr, ty = threadIdx.x / tpr;
+    const int strips = blockDim.x / tpr;
+    if (ty >= strips) return;
+    const int j0 = (blockIdx.x * strips + ty) * kStripRows;
+    if (j0 >= n1) return;
+    const int j1 = j0 + kStripRows < n1 ? j0 + kStripRows : n1;
+    const int c0 = tx * V;
+    const long long nx = g.nx;
+    const S* X = MODE == 1 ? nullptr : xin.d + (long long)b * xin.bs;
+    const S* Bp = bv.d + (long long)b * bv.bs;
+    S* O = out.d + (long long)b * out.bs;
+    auto vld = [&](const S* p, S* dst) {
+        VT v = *reinterpret_cast<const VT*>(p);
+        const S* q = reinterpret_cast<const S*>(&v);
+#pragma unroll
+        for (int t = 0; t < V; ++t) dst[t] = q[t];
+    };
+    // row j of x as V values plus the points left and right of the vector (zeros beyond the grid)
+    auto load_row = [&](int j, S* dst, S& l, S& r) {
+        if (j >= 0 && j < n1) {
+            vld(X + (long long)j * n0 + c0, dst);
+            l = c0 > 0 ? X[(long long)j * n0 + c0 - 1] : S(0);
+            r = c0 + V < n0 ? X[(long long)j * n0 + c0 + V] : S(0);
+        } else {
+#pragma unroll
+            for (int t = 0; t < V; ++t) dst[t] = S(0);
+            l = r = S(0);
+        }
+    };
+    S sr[V], pr[V], nr[V], sl = S(0), srr = S(0), pl = S(0), prr = S(0), nl = S(0), nrr = S(0);
+    if (MODE != 1) {
+        load_row(j0 - 1, sr, sl, srr);
+        load_row(j0, pr, pl, prr);
+    }
+    for (int j = j0; j < j1; ++j) {
+        if (MODE != 1) load_row(j + 1, nr, nl, nrr);
+        const long long p = (long long)j * n0 + c0;
+        S bq[V], ctr[V], res[V];
+        vld(Bp + p, bq);
+        vld(op.sten + 4 * nx + p, ctr);
+        if (MODE == 1) {
+#pragma unroll
+            for (int t = 0; t < V; ++t) res[t] = omega * bq[t] / ctr[t];
+        } else {
+            S st[9][V];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                if (k == 4) {
+#pragma unroll
+                    for (int t = 0; t < V; ++t) st[4][t] = ctr[t];
+                } else {
+                    vld(op.sten + (long long)k * nx + p, st[k]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                const S s0 = t == 0 ? sl : sr[t - 1], s2 = t == V - 1 ? srr : sr[t + 1];
+                const S p0 = t == 0 ? pl : pr[t - 1], p2 = t == V - 1 ? prr : pr[t + 1];
+                const S n0v = t == 0 ? nl : nr[t - 1], n2 = t == V - 1 ? nrr : nr[t + 1];
+                S acc = S(0);
+                acc += st[0][t] * s0;
+                acc += st[1][t] * sr[t];
+                acc += st[2][t] * s2;
+                acc += st[3][t] * p0;
+                acc += st[4][t] * pr[t];
+                acc += st[5][t] * p2;
+                acc += st[6][t] * n0v;
+                acc += st[7][t] * nr[t];
+                acc += st[8][t] * n2;
+                res[t] = MODE == 0 ? pr[t] + omega * (bq[t] - acc) / ctr[t] : bq[t] - acc;
+            }
+        }
+        VT ov;
+        S* oq = reinterpret_cast<S*>(&ov);
+#pragma unroll
+        for (int t = 0; t < V; ++t) oq[t] = res[t];
+        *reinterpret_cast<VT*>(O + p) = ov;
+        if (MODE != 1) {
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                sr[t] = pr[t];
+                pr[t] = nr[t];
+            }
+            sl = pl;
+            srr = prr;
+            pl = nl;
+            prr = nrr;
+        }
+    }
+}
+
 // Whether a level takes k_strip2d: 2D matrix-free with kappa = 1, unscaled storage, rows of whole
 // 16-byte vectors that tile a 256-thread block, and 16-byte aligned rows.
 template <class S>
@@ -491,6 +600,20 @@ inline bool strip_ok(const LevelOp<S>& op) {
                kStripThreads % (n0 / V) == 0;
     }
 }
+// Whether a level takes k_strip2d_st: a 2D stored 9-point stencil, unscaled storage, rows of whole
+// 16-byte vectors that tile a 256-thread block.
+template <class S>
+inline bool strip_st_ok(const LevelOp<S>& op) {
+    if constexpr (PT<S>::scaled) {
+        return false;
+    } else {
+        constexpr int V = Vec16<S>::n;
+        const int n0 = op.g.n0;
+        return !op.fine && op.g.d == 2 && op.ncoef == 9 && op.sten != nullptr && n0 % V == 0 &&
+               n0 / V <= kStripThreads && kStripThreads % (n0 / V) == 0;
+    }
+}
+
 template <class S>
 inline dim3 strip_grid(const LevelOp<S>& op, int B) {
     const int tpr = op.g.n0 / Vec16<S>::n;

@@ -736,6 +736,11 @@ class Precond : public PrecondBase {
                 else launch(k_strip2d<SI, 1>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, om);
                 return;
             }
+            if (kind == 2 && grid.y >= 16 && strip_st_ok(op)) {
+                if (x.d) launch(k_strip2d_st<SI, 0>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, om);
+                else launch(k_strip2d_st<SI, 1>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, om);
+                return;
+            }
         }
         launch_smooth_rows(kind, grid, block, op, pm, B, act, x, b, out, om);
     }
@@ -766,6 +771,10 @@ class Precond : public PrecondBase {
         if constexpr (!PT<SI>::scaled) {
             if (kind == 4 && grid.y >= 16 && strip_ok(op) && x.d) {
                 launch(k_strip2d<SI, 2>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, A(0));
+                return;
+            }
+            if (kind == 2 && grid.y >= 16 && strip_st_ok(op) && x.d) {
+                launch(k_strip2d_st<SI, 2>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, A(0));
                 return;
             }
         }
