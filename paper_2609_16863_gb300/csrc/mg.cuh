@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(kStripThreads) k_strip2d(LevelOp<S> op, int B,
 // skipped: the same value) and of k_smooth / k_residual: x + omega (b - A x) / a_PP.
 template <class S, int MODE>
 __global__ void __launch_bounds__(kStripThreads) k_strip2d_st(LevelOp<S> op, int B, const int* active, Vec<S> xin,
-                                                              Vec<S> bv, Vec<S> out, S omega) {
+                                                              Vec<S> bv, Vec<S> out, S omega, int rs) {
     pdl_prologue();
     static_assert(!PT<S>::scaled, "unscaled storage only");
     using VT = typename Vec16<S>::T;
@@ -499,9 +499,9 @@ __global__ void __launch_bounds__(kStripThreads) k_strip2d_st(LevelOp<S> op, int
     const int tx = threadIdx.x % tpr, ty = threadIdx.x / tpr;
     const int strips = blockDim.x / tpr;
     if (ty >= strips) return;
-    const int j0 = (blockIdx.x * strips + ty) * kStripRows;
+    const int j0 = (blockIdx.x * strips + ty) * rs;     // rs rows per strip (strip_st_rows)
     if (j0 >= n1) return;
-    const int j1 = j0 + kStripRows < n1 ? j0 + kStripRows : n1;
+    const int j1 = j0 + rs < n1 ? j0 + rs : n1;
     const int c0 = tx * V;
     const long long nx = g.nx;
     const S* X = MODE == 1 ? nullptr : xin.d + (long long)b * xin.bs;
@@ -612,6 +612,22 @@ inline bool strip_st_ok(const LevelOp<S>& op) {
         return !op.fine && op.g.d == 2 && op.ncoef == 9 && op.sten != nullptr && n0 % V == 0 &&
                n0 / V <= kStripThreads && kStripThreads % (n0 / V) == 0;
     }
+}
+
+// Rows per strip of k_strip2d_st: 8, halved (down to 2) while the batch gives fewer than 1024 blocks,
+// so that a coarse level (few rows per item) still spreads over every SM; the shorter strips re-read
+// more halo rows, from L1/L2.
+template <class S>
+inline int strip_st_rows(const LevelOp<S>& op, int B) {
+    const int strips = kStripThreads / (op.g.n0 / Vec16<S>::n);
+    int rs = kStripRows;
+    while (rs > 2 && (long long)B * ((op.g.n1 + strips * rs - 1) / (strips * rs)) < 1024) rs /= 2;
+    return rs;
+}
+template <class S>
+inline dim3 strip_st_grid(const LevelOp<S>& op, int B, int rs) {
+    const int strips = kStripThreads / (op.g.n0 / Vec16<S>::n);
+    return dim3((unsigned)((op.g.n1 + strips * rs - 1) / (strips * rs)), (unsigned)B, 1);
 }
 
 template <class S>

@@ -737,8 +737,9 @@ class Precond : public PrecondBase {
                 return;
             }
             if (kind == 2 && grid.y >= 16 && strip_st_ok(op)) {
-                if (x.d) launch(k_strip2d_st<SI, 0>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, om);
-                else launch(k_strip2d_st<SI, 1>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, om);
+                const int rs = strip_st_rows(op, B);
+                if (x.d) launch(k_strip2d_st<SI, 0>, strip_st_grid(op, B, rs), kStripThreads, 0, st(), op, B, act, x, b, out, om, rs);
+                else launch(k_strip2d_st<SI, 1>, strip_st_grid(op, B, rs), kStripThreads, 0, st(), op, B, act, x, b, out, om, rs);
                 return;
             }
         }
@@ -774,7 +775,8 @@ class Precond : public PrecondBase {
                 return;
             }
             if (kind == 2 && grid.y >= 16 && strip_st_ok(op) && x.d) {
-                launch(k_strip2d_st<SI, 2>, strip_grid(op, B), kStripThreads, 0, st(), op, B, act, x, b, out, A(0));
+                const int rs = strip_st_rows(op, B);
+                launch(k_strip2d_st<SI, 2>, strip_st_grid(op, B, rs), kStripThreads, 0, st(), op, B, act, x, b, out, A(0), rs);
                 return;
             }
         }
