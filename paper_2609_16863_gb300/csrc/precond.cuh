@@ -929,11 +929,20 @@ class Precond : public PrecondBase {
         for (int t = 0; t < s; ++t) {
             int i = transpose ? s - 1 - t : t;
             const double* coef = (transpose ? h->d_LDb : h->d_LDf) + i * s;
+            Vec<SI> Zi = shift_vec(Z, (long long)i * g.nx, g.n0);
+            if constexpr (std::is_same<SP, SI>::value && !PT<SI>::scaled) {
+                // the sweep's first stage has no coupling (L is unit lower triangular): its right-hand
+                // side is V_i itself, which the shifted solve reads in place (the copy into mgb would
+                // store the same values)
+                if (t == 0) {
+                    AAO_TRY(mg_solve(i, B, act, shift_vec(V, (long long)i * g.nx, g.n0), Zi));
+                    continue;
+                }
+            }
             bytes_hint(1.0 * nact * g.nx * (sizeof(SP) + (transpose ? s - 1 - i : i) * sizeof(SI) + sizeof(SI)));
             launch(k_rana_rhs<SP, SI>, pt_grid(pm0, g.R, B), pt_block(pm0), 0, st(), g, pm0, B, act, V, i, Z, s,
                    coef, (A)h->tau, sopA, mgb);
             AAO_LAUNCH_CHECK();
-            Vec<SI> Zi = shift_vec(Z, (long long)i * g.nx, g.n0);
             AAO_TRY(mg_solve(i, B, act, mgb, Zi));
         }
         return AAO_OK;
