@@ -19,7 +19,7 @@ from typing import Dict, Iterable, Optional, Sequence, Tuple
 from .api import Solver
 
 
-def mgrit_candidates(nt: int, factors: Iterable[int] = (4, 6, 8, 10, 12, 16, 32)) -> list:
+def mgrit_candidates(nt: int, factors: Iterable[int] = (4, 6, 8, 9, 10, 11, 12, 16, 32)) -> list:
     """0 (substitution) and every factor m with at least two C-point intervals (m need not divide
     nt: the steps after the last C-point form a shorter final interval)."""
     return [0] + [m for m in factors if nt // m >= 2]
