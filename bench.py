@@ -129,7 +129,7 @@ def batched_arm(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": f"f64/{args.prec}",
             "data": "synthetic", "config": {"workload": "batched64", "problems": len(ws), "n_st_total": nst,
                                             "schur": f"MGRIT m = {8 if args.mgrit_m < 0 else args.mgrit_m} "
-                                                     f"where it divides nt",
+                                                     f"where nt has two or more intervals",
                                             "execution": "one host thread and stream per problem"},
             "dofs_its_per_s": sum(S.n_st * i for S, i in zip(solvers, its)) / t,
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
