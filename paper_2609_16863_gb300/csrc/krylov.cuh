@@ -279,6 +279,11 @@ template <class SZ, class A>
 __global__ void __launch_bounds__(kPtMaxThreads) k_theta(Geo g, PtMap pm, int B, const int* active, Vec<SZ> Z, A* wv,
                                                 long long wbs, int s, const double* coef, A tau, SpaceOp<A> sop) {
     pdl_prologue();
+    // tau a_ij in the arithmetic type, once per block (the products the per-point sum uses)
+    __shared__ A tc[kMaxS * kMaxS];
+    for (int t = threadIdx.y * blockDim.x + threadIdx.x; t < s * s; t += blockDim.x * blockDim.y)
+        tc[t] = tau * (A)coef[t];
+    __syncthreads();
     PtPos q = pt_pos(pm, B, g.R, active);
     if (!q.valid) return;
     const long long row = q.row;
@@ -294,7 +299,7 @@ __global__ void __launch_bounds__(kPtMaxThreads) k_theta(Geo g, PtMap pm, int B,
         for (int i = 0; i < s; ++i) {
             View<SZ> zi = view_of(Z, q.b, (long long)i * g.nx, g.n0);
             A acc = (A)op_M(zi, g, sop, row, j, k, c);
-            for (int jj = 0; jj < s; ++jj) acc += tau * (A)coef[i * s + jj] * kz[jj];
+            for (int jj = 0; jj < s; ++jj) acc += tc[i * s + jj] * kz[jj];
             out[(long long)i * g.nx + c] = acc;
         }
     }
