@@ -60,9 +60,10 @@ class Info:
 
 class Solver:
     """Handle for one problem: grid n (interior points per axis), final time T,
-    nt steps, an RK tableau (A, b, c), optional nodal diffusivity kappa.  mgrit_m > 0
-    (a divisor of nt) replaces S_tilde's forward substitution by one two-level MGRIT
-    iteration with coarsening factor mgrit_m; precond_side="left" runs Algorithm 1 with
+    nt steps, an RK tableau (A, b, c), optional nodal diffusivity kappa.  mgrit_m in 2..nt
+    replaces S_tilde's forward substitution by one two-level MGRIT iteration with coarsening
+    factor mgrit_m (C-points at its multiples; a shorter final interval where it does not
+    divide nt; tune.tune_mgrit picks one by timing); precond_side="left" runs Algorithm 1 with
     P_L = P_tilde, P_R = I instead of the right-preconditioned FGMRES.  relax_matvec = ell > 0
     lets late outer iterations keep an FP32 product A z_k whose error bound is within the
     inexact-Krylov allowance ell tol ||b|| / (restart |g_k|) (aao_options.relax_matvec)."""

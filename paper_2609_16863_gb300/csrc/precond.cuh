@@ -1254,8 +1254,8 @@ class Precond : public PrecondBase {
     // thread-block cluster: one launch then holds every interval's clusters): F-relaxation as
     // batched steps over the mg_nc intervals from z_0 = w_0 and zero C-points, the C-point
     // residuals, the coarse error recurrence e_c = Phi_c(e_{c-1}) + r_c by substitution with step
-    // m tau, the C-point correction z_{cm} += e_c and a final F-relaxation.  w is in wbuf; z_0
-    // is set by the caller.
+    // m tau, the C-point correction z_{cm} += e_c and a final F-relaxation (which also relaxes the
+    // shorter last interval when m does not divide nt).  w is in wbuf; z_0 is set by the caller.
     aao_status mgrit_batched_forward(double* z) {
         const long long nx = h->g.nx;
         const int m = mg_m, nc = mg_nc;
